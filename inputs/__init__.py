@@ -1,0 +1,12 @@
+"""Seeded synthetic inputs shared by the oracle and the GPU path.
+
+This package holds only input generators: the jittered Kuhn tetrahedral mesh
+family (6 tetrahedra per hexahedron) and closed-form velocity fields used as
+initial and Dirichlet boundary data.  It contains none of the discretisation's
+arithmetic (no bases, quadrature, blocks, solvers).
+"""
+from .mesh import kuhn_mesh, splitmix64_doubles
+from .fields import beltrami_velocity, beltrami_pressure, BeltramiParams, SolenoidalModes
+
+__all__ = ["kuhn_mesh", "splitmix64_doubles", "beltrami_velocity", "beltrami_pressure",
+           "BeltramiParams", "SolenoidalModes"]
