@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the staggered space-time DG pressure-correction time step on one GB300.
+
+Workload (default): unit cube, 24^3 hexahedra x 6 = 82,944 jittered tetrahedra (seed 0),
+p = 3, p_t = 1 (N = 20, Nst = 40, 3,317,760 pressure DoFs), Beltrami data (a = pi/4,
+d = pi/2), nu = 0.01, dt = 0.005, 3 Picard iterations per step, pressure solves to a
+1e-10 relative residual.  A "step" is one full time step (stdg_step: averaging, convection,
+viscous solves, pressure right-hand side, pressure solve, velocity update, 3 times).
+
+Metric: seconds per time step with the chosen solver (Kronecker-decoupled block CG), next
+to plain FP64 GMRES(50); the operator kernel's achieved throughput is reported as a
+roofline against the FP64 pipe (its bound on sm_103a) and against HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s/time-step at 1e-10 residual (chosen vs plain FP64 GMRES); matvec HBM GB/s"
+WORKLOADS = {
+    "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
+    "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50),
+}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
+
+
+def nbasis(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def workload_name(w):
+    ne = 6 * w["n"] ** 3
+    N = nbasis(w["p"]); Nst = N * (w["pt"] + 1)
+    return (f"Kuhn {w['n']}^3 hex x 6 = {ne:,} tets, p={w['p']}, p_t={w['pt']} ({ne * Nst:,} pressure DoFs), "
+            f"Beltrami data, nu={w['nu']}, dt={w['dt']}, {w['npic']} Picard iterations/step, tol {w['tol']:g}")
+
+
+def mesh_counts(n):
+    ne = 6 * n ** 3; nb = 12 * n * n
+    return ne, (4 * ne - nb) // 2, nb
+
+
+def operator_cost(w):
+    """Algorithmic bytes and flops of one five-point operator application (assembled form:
+    symmetric diagonal blocks counted packed, every off-diagonal block once, x read once, y
+    written once; flops = 2 Ng per applied block entry)."""
+    ne, nint, _ = mesh_counts(w["n"])
+    N = nbasis(w["p"]); Ng = w["pt"] + 1
+    entries = ne * N * (N + 1) // 2 + nint * N * N
+    bytes_alg = 8 * entries + 2 * 8 * ne * N * Ng
+    flops = 2 * Ng * (ne * N * N + 2 * nint * N * N)
+    return bytes_alg, flops
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, dev):
+        self.dev, self.lines, self.proc = dev, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_operator_sample(w, reps=3, n_sample=3):
+    """The oracle's matrix-free pressure operator (as it stands) on a small mesh of the same
+    family, degrees and time step; returns seconds per application scaled to the full mesh
+    by the number of interior faces."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from inputs import kuhn_mesh
+    from oracle import operators as ops
+    from oracle.blocks import SpaceTimeDG
+    from oracle.mesh import Mesh
+    v, t = kuhn_mesh(n_sample, seed=0)
+    d = SpaceTimeDG(Mesh(v, t), w["p"], w["pt"], w["dt"])
+    for j in range(d.mesh.nf):
+        d.face_blocks(j)                                       # precompute (untimed)
+    x = np.random.default_rng(0).standard_normal((d.mesh.ne, d.Nst))
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ops.pressure_apply(d, x)
+        times.append(time.perf_counter() - t0)
+    nint_s = int(d.mesh.interior.sum())
+    _, nint, _ = mesh_counts(w["n"])
+    return float(np.median(times)) * nint / nint_s, nint_s
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        n = 1
+    return 1 if os.environ.get("OMP_NUM_THREADS") == "1" else n
+
+
+def reference_arm(args, w, world, rank):
+    if rank != 0:
+        return
+    counts = json.load(open(COUNTS_FILE)) if os.path.exists(COUNTS_FILE) else None
+    if counts is None or counts.get("workload") != workload_name(w):
+        print(json.dumps({"impl": "reference", "unavailable": "no operator-application count recorded for this "
+                          "workload (profiles/bench_operator_counts.json)"}))
+        return
+    per_step_ops = counts["operator_applications_per_step"]
+    for _ in range(args.warmup):
+        oracle_operator_sample(w, reps=1)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        s_op, nint_s = oracle_operator_sample(w, reps=1)
+        vals.append(s_op * per_step_ops)
+    wall = time.perf_counter() - t_all
+    v = float(np.median(vals))
+    sample = (f"oracle matrix-free pressure operator on the {nint_s}-interior-face 3^3 mesh of the same family/p/p_t, "
+              f"scaled to {mesh_counts(w['n'])[1]:,} interior faces x {per_step_ops} operator applications per step "
+              f"(count measured by the GPU arm on this workload); other per-step work not included")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+                      "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": workload_name(w), "parallelism": "replicas"},
+                      "cpu_baseline": {"value": v, "unit": "s/step", "cores": cpu_threads(), "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                      "wall_s": wall}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--gmres-steps", type=int, default=1)
+    ap.add_argument("--gmres-max-iters", type=int, default=30000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"])
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, w, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_1601_07384_gb300.build import build
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_1601_07384_gb300 as g
+    from inputs import kuhn_mesh
+
+    v, t = kuhn_mesh(w["n"], seed=0)
+    mesh = g.Mesh(v, t)
+    ref = g.Reference(w["p"], w["pt"])
+    solver = g.Solver(mesh, ref, w["dt"], precision=args.precision, restart=w["restart"], max_iters=200000)
+    fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
+    solver.set_initial(fld)
+    solver.set_boundary(fld)
+    stream = solver.stream
+    for _ in range(args.warmup):
+        solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K steps with the chosen solver, inputs resident in HBM
+    solver.profile(True)
+    stats = []
+    with ClockSampler(local) as clk:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"]))
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof = solver.profile_read()
+    solver.profile(False)
+    t_dev = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+    ms = float(t_dev.item())
+    s_per_step = ms / 1e3 / args.steps
+
+    # ---- end to end through the C ABI with host buffers (state in from / out to pinned host memory)
+    P0, V0, t0 = solver.get_state()
+    Ph = torch.empty(P0.numel(), dtype=torch.float64).pin_memory()
+    Vh = torch.empty(V0.numel(), dtype=torch.float64).pin_memory()
+    Ph.copy_(P0); Vh.copy_(V0)
+    lib = g._lib.load()
+    import ctypes as C
+    tcur = C.c_double(t0)
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0, tcur.value))
+        solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"])
+        g._lib.check(lib.stdg_get_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0,
+                                        C.byref(tcur)))
+    barrier()
+    e2e = (time.perf_counter() - te0) / args.steps
+
+    # ---- plain FP64 GMRES(50) on the same step (the paper's solver), from the same state
+    gm = None
+    if args.gmres_steps > 0:
+        solver.set_state(P0, V0, t0)
+        gsolver = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=args.gmres_max_iters)
+        gsolver.set_boundary(fld)
+        gsolver.set_state(P0, V0, t0)
+        gts = []
+        ok = True
+        for _ in range(args.gmres_steps):
+            torch.cuda.synchronize()
+            tg0 = time.perf_counter()
+            try:
+                st = gsolver.step(w["nu"], w["npic"], method="gmres", tol=w["tol"])
+            except g.StdgError as exc:
+                ok = False
+                st = {"error": str(exc)}
+            torch.cuda.synchronize()
+            gts.append(time.perf_counter() - tg0)
+        gm = {"s_per_step": float(np.median(gts)), "converged": ok,
+              "max_iters_per_solve": args.gmres_max_iters,
+              "press_iters": st.get("press_iters") if ok else None}
+        del gsolver
+
+    # ---- roofline of the operator kernel
+    bytes_alg, flops = operator_cost(w)
+    op_launch_ms = prof["operator_ms"] / max(prof["operator_launches"], 1)
+    tflops = flops / (op_launch_ms * 1e-3) / 1e12
+    gbs = bytes_alg / (op_launch_ms * 1e-3) / 1e9
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    ops_per_step = prof["operator_launches"] / args.steps
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "operator_traffic.json")
+    if os.path.exists(tf):
+        tr = json.load(open(tf))
+        if tr.get("workload") == workload_name(w) and tr.get("precision") == args.precision:
+            traffic = tr.get("dram_bytes_per_launch")
+
+    out = {
+        "metric": METRIC, "value": s_per_step * 1.0, "unit": "s/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s_per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (fp32-pair products)",
+        "data": "synthetic",
+        "config": {"workload": workload_name(w), "solver": "kron_cg (block CG on the Ng decoupled SPD systems)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_apply (five-point block operator)",
+                     "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                             "algorithmic_bytes_per_launch": bytes_alg},
+                     "flops_per_launch": flops, "avg_launch_ms": op_launch_ms,
+                     "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (measured 1.20 TFLOP/s)"},
+        "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(P0.numel() + V0.numel()) * 8,
+                "d2h_bytes_per_step": int(P0.numel() + V0.numel()) * 8},
+        "gpu_launches": int(prof["kernel_launches"]),
+        "operator_applications_per_step": ops_per_step,
+        "press_iters": [s["press_iters"] for s in stats],
+        "visc_iters": [s["visc_iters"] for s in stats],
+        "max_divergence": max(s["max_divergence"] for s in stats),
+        "plain_gmres": gm,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        s_op, nint_s = oracle_operator_sample(w)
+        out["cpu_baseline"] = {
+            "value": s_op * ops_per_step, "unit": "s/step", "cores": cpu_threads(), "kind": "oracle",
+            "sample": (f"oracle matrix-free pressure operator on the {nint_s}-interior-face 3^3 mesh of the same "
+                       f"family/p/p_t, scaled to {mesh_counts(w['n'])[1]:,} interior faces x {ops_per_step:.0f} "
+                       f"operator applications per step; other per-step work not included")}
+    if rank == 0:
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        with open(os.path.join(ROOT, "gpurun_out", f"bench_counts_{args.workload}.json"), "w") as f:
+            json.dump({"workload": workload_name(w), "operator_applications_per_step": ops_per_step}, f)
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * stdg.h -- C ABI of the GB300 (sm_103a) implementation of the staggered semi-implicit
+ * space-time DG pressure-correction scheme for the 3D incompressible Navier-Stokes
+ * equations on tetrahedral meshes (Tavelli & Dumbser, arXiv:1601.07384).
+ *
+ * Conventions shared by every call
+ *  - All floating point data is IEEE binary64 unless a call says otherwise.
+ *  - Pointers named *_dev are raw CUDA device pointers on the solver's device; pointers
+ *    named *_host are host pointers.  The caller owns every buffer it passes; the library
+ *    reads inputs during the call (stream-ordered for device buffers) and never keeps them.
+ *  - The library owns the objects it returns and the device arrays inside them; free them
+ *    with the matching *_destroy call.
+ *  - Device work is issued on the CUDA stream given to stdg_solver_create, in order.
+ *  - Nothing aborts or throws across this boundary: every call returns a stdg_status; on a
+ *    negative status stdg_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread).  There is no CPU fallback: a missing GPU is STDG_ECUDA.
+ *  - Index conventions (Sec. 2.2-2.3 of the paper):
+ *      N  = (p+1)(p+2)(p+3)/6 spatial basis functions, Ng = p_t + 1 time functions,
+ *      Nst = N * Ng; a space-time coefficient (time a, space k) sits at a*N + k.
+ *      Tet basis: orthonormal Dubiner on {xi,eta,zeta >= 0, xi+eta+zeta <= 1}; multi-index
+ *      order "for n=0..p, i=0..n, j=0..n-i: (i, j, n-i-j)".  Time basis: orthonormal
+ *      Legendre on [0,1].  Dual basis: the paper's scaled Taylor monomials (Eq. bf_2),
+ *      Gram-Schmidt orthonormalised on each dual cell in the same multi-index order.
+ *      Faces are numbered by increasing (l(j), local face of l(j)), l(j) = lower tet id;
+ *      local face f of a tet is the face opposite its local vertex f.
+ *  - Array layouts:  pressure  P[ne][Ng][N];  velocity on dual cells V[nf][3][Ng][N];
+ *      averaged velocity on tets Vbar[ne][3][Ng][N].
+ */
+#ifndef STDG_H
+#define STDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stdg_mesh stdg_mesh;
+typedef struct stdg_ref stdg_ref;
+typedef struct stdg_solver stdg_solver;
+
+typedef enum {
+  STDG_OK = 0,
+  STDG_EINVAL = -1,       /* bad argument                                              */
+  STDG_ENOMEM = -2,       /* host or device allocation failed                          */
+  STDG_ECUDA = -3,        /* a CUDA runtime call failed (including: no usable GPU)     */
+  STDG_ENOCONV = -4,      /* Krylov iteration cap reached; stats are filled in         */
+  STDG_EMESH = -5,        /* inverted / degenerate tet or non-manifold face            */
+  STDG_ENAN = -6,         /* a non-finite value appeared in a solve                    */
+  STDG_ETIMEOUT = -7,     /* reserved: a bounded device wait gave up                   */
+  STDG_EUNSUPPORTED = -8  /* degree or option outside what this build supports         */
+} stdg_status;
+
+/* Krylov methods for stdg_solve.
+ *  STDG_SOLVER_GMRES : restarted GMRES(m) on the full space-time pressure operator with
+ *                      classical Gram-Schmidt applied twice, as the paper's matrix-free,
+ *                      unpreconditioned GMRES (abstract; Sec. 2.4, 2.7).
+ *  STDG_SOLVER_CG    : conjugate gradients on -A; only for p_t = 0 (Sec. 2.7, Cor. 1-2).
+ *  STDG_SOLVER_KRON_CG: the same pinned system solved exactly as Ng decoupled symmetric
+ *                      positive definite systems: with the orthonormal bases used here the
+ *                      operator of Eq. CS_19 factors as A = A_sp (x) dt^2 K^-1, so
+ *                      A x = b  <=>  A_sp X = B K^T / dt^2 column by column (block CG, all
+ *                      columns share each operator launch).  The stopping test is on the
+ *                      residual of the full system, as for the other methods.            */
+enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2 };
+
+/* Precision of the operator blocks used inside the Krylov iteration (stdg_solver_options).
+ *  STDG_PREC_FP64   : blocks and arithmetic in binary64.
+ *  STDG_PREC_DF32   : binary64 blocks and vectors, products formed in pairs of binary32
+ *                     ("double-float", ~48-bit significand) because sm_103a's binary64
+ *                     pipe is ~1/58 of its binary32 rate; results agree with STDG_PREC_FP64
+ *                     to ~1e-14 relative per operator application.                       */
+enum { STDG_PREC_FP64 = 0, STDG_PREC_DF32 = 1 };
+
+typedef struct {
+  int iterations;          /* Krylov iterations (operator applications in the loop)   */
+  int restarts;            /* GMRES restarts                                          */
+  double rel_residual;     /* ||b - A x|| / ||b|| of the returned x                   */
+  double seconds;          /* wall time of the call                                   */
+} stdg_solve_stats;
+
+typedef struct {
+  int picard;              /* Picard iterations done                                  */
+  int press_iters[8];      /* pressure Krylov iterations per Picard iteration         */
+  int visc_iters[8];       /* viscous Krylov iterations (sum over 3 components)       */
+  double press_residual[8];/* final relative residual of each pressure solve          */
+  double seconds;          /* wall time of the step                                   */
+  double max_divergence;   /* max_i |Sum_j D_ij v_j| over unpinned tets after the step */
+} stdg_step_stats;
+
+/* Velocity data kinds for initial and Dirichlet boundary values (evaluated on the device).
+ *  STDG_FIELD_ZERO     : v = 0 (no-slip walls).
+ *  STDG_FIELD_CONSTANT : v = (c0, c1, c2).
+ *  STDG_FIELD_BELTRAMI : Ethier-Steinman unsteady solution, params (a, d, nu):
+ *      u = -a [e^{ax} sin(ay+dz) + e^{az} cos(ax+dy)] e^{-nu d^2 t}, v, w by cyclic shift. */
+enum { STDG_FIELD_ZERO = 0, STDG_FIELD_CONSTANT = 1, STDG_FIELD_BELTRAMI = 2 };
+typedef struct { int kind; double c[3]; double a, d, nu; } stdg_field;
+
+/* ---------------------------------------------------------------- mesh (Sec. 2.2) */
+/* Build the primary mesh and its face-based dual grid: faces from sorted vertex triples,
+ * l(j) = lower tet id, r(j) = higher (-1 on the boundary), unit normals n_j from l to r,
+ * sub-tetrahedra T_{i,j} (face j + barycentre of T_i).  verts_host[nv][3], tets_host[ne][4]
+ * (0-based vertex ids, any orientation: a negative orientation is rejected as STDG_EMESH,
+ * as are zero volumes and faces shared by more than two tets).  Host-only; no GPU needed. */
+stdg_status stdg_mesh_create(const double* verts_host, int64_t nv, const int64_t* tets_host,
+                             int64_t ne, stdg_mesh** out);
+void stdg_mesh_destroy(stdg_mesh* mesh);
+stdg_status stdg_mesh_info(const stdg_mesh* mesh, int64_t* ne, int64_t* nfaces,
+                           int64_t* ninterior, int64_t* nboundary);
+/* Face table in face order: left[nf], right[nf] (-1 = boundary), lface[nf], rface[nf]
+ * (local face indices, -1 on the boundary).  Any output pointer may be NULL. */
+stdg_status stdg_mesh_faces(const stdg_mesh* mesh, int64_t* left_host, int64_t* right_host,
+                            int32_t* lface_host, int32_t* rface_host);
+
+/* ------------------------------------------------ reference matrices (Sec. 2.3-2.4) */
+/* Quadrature rules, Dubiner / Legendre tables and the time matrices
+ * K_ab = gamma_a(1) gamma_b(1) - int_0^1 gamma_a' gamma_b (from Eqs. MD_2, MD_2_2).
+ * Supported: 0 <= p <= 4, 0 <= p_t <= 4 (STDG_EUNSUPPORTED otherwise).  Host-only. */
+stdg_status stdg_reference_matrices(int p, int p_t, stdg_ref** out);
+void stdg_ref_destroy(stdg_ref* ref);
+/* K into K_host[Ng*Ng] (row a, column b). */
+stdg_status stdg_ref_time_matrix(const stdg_ref* ref, double* K_host);
+/* Evaluate the reference tet basis (Sec. 2.3) at n points xi_host[n][3] of the reference
+ * tetrahedron: phi_host[n][N] and reference gradients dphi_host[n][3][N] (either may be NULL).
+ * Points on the edge eta + zeta = 1 or at zeta = 1 are outside the collapsed map: EINVAL. */
+stdg_status stdg_ref_eval(const stdg_ref* ref, const double* xi_host, int64_t n, double* phi_host,
+                          double* dphi_host);
+/* The tetrahedron quadrature rule with `npts1d` points per direction (collapsed Gauss-Jacobi
+ * product, exact to total degree 2*npts1d-1): xi_host[npts1d^3][3], w_host[npts1d^3], weights
+ * summing to 1/6.  Host-only. */
+stdg_status stdg_tet_rule(int npts1d, double* xi_host, double* w_host);
+
+/* ------------------------------------------------------------------ solver objects */
+typedef struct {
+  int precision;           /* STDG_PREC_FP64 (default) or STDG_PREC_DF32              */
+  int restart;             /* GMRES restart length m (default 50)                     */
+  int max_iters;           /* cap on Krylov iterations per solve (default 200000)     */
+} stdg_solver_options;
+
+/* Upload mesh and reference tables to the current CUDA device and build every per-face
+ * and per-tet coefficient block on it (the paper's preprocessing step, Sec. 4):
+ * orthonormal dual basis, Q_{i,j} (Eq. MD_6, spatial part), M_{i,j} (Eq. vis3), and the
+ * assembled five-point spatial blocks B_i and A_{l r} of Sum_j D M^-1 Q (Eq. CS_19).
+ * cuda_stream may be NULL (default stream).  opts may be NULL (defaults).
+ * Device memory: ~ (ne + nf) * N^2 * 8 * 4 bytes + nf * N^2 * 8 * 9 bytes. */
+stdg_status stdg_solver_create(const stdg_mesh* mesh, const stdg_ref* ref, double dt,
+                               const stdg_solver_options* opts, void* cuda_stream,
+                               stdg_solver** out);
+void stdg_solver_destroy(stdg_solver* s);
+/* Change the time step (rebuilds only the Ng x Ng time factor dt^2 K^-1). */
+stdg_status stdg_set_dt(stdg_solver* s, double dt);
+
+/* ---------------------------------------------------------------- hot-path kernels */
+/* y = A x, the five-point block pressure operator of Eq. CS_19 / A2_mod (left-hand side):
+ * (A x)_i = Sum_{j in S_i, interior} D_ij M_j^-1 (Q_ij x_i + Q_{p(i,j),j} x_{p(i,j)}).
+ * Boundary dual cells carry prescribed velocity and add nothing to A.  pinned != 0:
+ * the pressure is fixed at one point (abstract, Sec. 2.7) by eliminating the constant
+ * Dubiner mode of tet 0 for every time function: x there is read as 0 and y there = -x.
+ * x_dev, y_dev: P layout, ne*Nst doubles each, must not overlap. */
+stdg_status stdg_pressure_apply(stdg_solver* s, const double* x_dev, double* y_dev, int pinned);
+
+/* b = Sum_{j in S_i} D_ij F_j over all four faces of each tet (Eq. A2_mod right-hand side,
+ * Eq. CS_15 left-hand side), with D_ij = -Q_ij^T.  F_dev: V layout (nf*3*Nst), b_dev: P
+ * layout.  pinned != 0 zeroes b at the pinned entries. */
+stdg_status stdg_pressure_rhs(stdg_solver* s, const double* F_dev, double* b_dev, int pinned);
+
+/* Velocity update of Eq. A3_mod: v_j = F_j - M_j^-1 (Q_rj dp_r + Q_lj dp_l) on interior
+ * faces; boundary dual cells copy F_j.  F_dev, V_dev: V layout; dp_dev: P layout.
+ * V_dev may equal F_dev (in place). */
+stdg_status stdg_velocity_update(stdg_solver* s, const double* F_dev, const double* dp_dev,
+                                 double* V_dev);
+
+/* Solve the pinned pressure system A x = b (Eq. A2_mod) to ||b - A x|| <= tol ||b||,
+ * starting from x = 0, with `method` (STDG_SOLVER_*).  b_dev, x_dev: P layout.
+ * Returns STDG_ENOCONV when max_iters is reached (x holds the last iterate). */
+stdg_status stdg_solve(stdg_solver* s, const double* b_dev, double* x_dev, double tol,
+                       int method, stdg_solve_stats* stats);
+
+/* ---------------------------------------------------------------- time stepping */
+/* Initial velocity: spatial L2 projection of `field` at t = 0 onto every dual cell
+ * (constant in time), pressure 0, time t = 0. */
+stdg_status stdg_set_initial(stdg_solver* s, const stdg_field* field);
+/* Dirichlet velocity on the boundary (all boundary faces), evaluated each step. */
+stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* field);
+/* One time step t -> t + dt of the Picard pressure-correction algorithm (Sec. 2.6, steps
+ * 0-6), n_picard Picard iterations, viscosity nu; pressure solves with `method` to `tol`,
+ * viscous solves (Eq. A1_mod) with CG (p_t = 0) or GMRES to `tol`.  stats may be NULL. */
+stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
+                      stdg_step_stats* stats);
+/* Copy the state out / in: P (ne*Nst) and V (nf*3*Nst), device or host pointers per
+ * on_device; either pointer may be NULL.  t_out may be NULL. */
+stdg_status stdg_get_state(const stdg_solver* s, double* P, double* V, int on_device, double* t_out);
+stdg_status stdg_set_state(stdg_solver* s, const double* P, const double* V, int on_device, double t);
+/* Basis-independent velocity moments U[nf][2][3][Ng][N]: for each face j and each side s
+ * (l, then r; r slot zero on the boundary) U = int_{T_{s,j}^st} phi~^(s) v_h (the
+ * M_{i,j} v_j product of Eq. vis3).  V_dev: V layout, U_dev: nf*2*3*Nst doubles. */
+stdg_status stdg_velocity_moments(stdg_solver* s, const double* V_dev, double* U_dev);
+
+/* ---------------------------------------------------------------- profiling */
+typedef struct {
+  int64_t kernel_launches;   /* CUDA kernels this library launched since stdg_profile      */
+  int64_t operator_launches; /* five-point operator launches (pressure and viscous)        */
+  double operator_ms;        /* summed CUDA-event time of the operator launches (enabled)  */
+} stdg_profile_stats;
+/* Reset the counters; enable != 0 also records a CUDA event pair around every operator
+ * launch on the solver's stream (adds two event records per launch). */
+stdg_status stdg_profile(stdg_solver* s, int enable);
+/* Synchronise the solver's stream and read the counters. */
+stdg_status stdg_profile_read(stdg_solver* s, stdg_profile_stats* out);
+
+/* ---------------------------------------------------------------- inspection */
+/* Copy per-face spatial blocks to host arrays (any may be NULL):
+ *  Q_host[nf][2][3][N][N]: Q^sp_{s,j}[c][m][l] = int_{T_sj} psi_m d_c phi_l - sigma n_c int_{Gamma_j} psi_m phi_l
+ *     (Eq. MD_6 without the time factor); on a boundary face slot 1 holds the volume part.
+ *  Mij_host[nf][2][N][N]: int_{T_sj} phi_k psi_l.   Aoff_host[nf][N][N], Bdiag_host[ne][N][N]. */
+stdg_status stdg_get_blocks(const stdg_solver* s, double* Q_host, double* Mij_host,
+                            double* Aoff_host, double* Bdiag_host);
+
+const char* stdg_last_error(void);
+const char* stdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STDG_H */

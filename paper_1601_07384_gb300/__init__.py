@@ -1,0 +1,229 @@
+"""GB300 (sm_103a) implementation of the staggered space-time DG pressure-correction path
+(Tavelli & Dumbser, arXiv:1601.07384) behind the C ABI of include/stdg.h.
+
+This module only marshals arguments: every step of the path runs in libstdg.so's CUDA kernels.
+PyTorch supplies device memory and the CUDA stream.  There is no CPU fallback: if the library
+or a GPU is missing, the calls raise.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import FIELD, PREC, SOLVER, Field, SolveStats, SolverOptions, StdgError, StepStats
+
+__all__ = ["Mesh", "Reference", "Solver", "StdgError", "beltrami", "constant", "zero", "nbasis"]
+
+
+def nbasis(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def beltrami(a=np.pi / 4, d=np.pi / 2, nu=0.1):
+    f = Field(); f.kind = FIELD["beltrami"]; f.a = a; f.d = d; f.nu = nu
+    return f
+
+
+def constant(u):
+    f = Field(); f.kind = FIELD["constant"]
+    for k in range(3):
+        f.c[k] = float(u[k])
+    return f
+
+
+def zero():
+    f = Field(); f.kind = FIELD["zero"]
+    return f
+
+
+class Mesh:
+    """Primary tetrahedral mesh and its face-based dual grid (stdg_mesh_create)."""
+
+    def __init__(self, verts, tets):
+        lib = _lib.load()
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tets, dtype=np.int64)
+        h = C.c_void_p()
+        _lib.check(lib.stdg_mesh_create(v.ctypes.data_as(_lib.DP), v.shape[0], t.ctypes.data_as(_lib.I64P),
+                                        t.shape[0], C.byref(h)))
+        self._h = h
+        ne, nf, ni, nb = (C.c_int64() for _ in range(4))
+        _lib.check(lib.stdg_mesh_info(h, C.byref(ne), C.byref(nf), C.byref(ni), C.byref(nb)))
+        self.ne, self.nf, self.ninterior, self.nboundary = ne.value, nf.value, ni.value, nb.value
+
+    def faces(self):
+        lib = _lib.load()
+        l = np.empty(self.nf, np.int64); r = np.empty(self.nf, np.int64)
+        fl = np.empty(self.nf, np.int32); fr = np.empty(self.nf, np.int32)
+        _lib.check(lib.stdg_mesh_faces(self._h, l.ctypes.data_as(_lib.I64P), r.ctypes.data_as(_lib.I64P),
+                                       fl.ctypes.data_as(_lib.I32P), fr.ctypes.data_as(_lib.I32P)))
+        return l, r, fl, fr
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib._lib is not None:
+            _lib._lib.stdg_mesh_destroy(self._h)
+            self._h = None
+
+
+class Reference:
+    """Reference quadrature / basis tables and the time matrix K (stdg_reference_matrices)."""
+
+    def __init__(self, p, pt):
+        lib = _lib.load()
+        h = C.c_void_p()
+        _lib.check(lib.stdg_reference_matrices(int(p), int(pt), C.byref(h)))
+        self._h, self.p, self.pt = h, p, pt
+        self.N, self.Ng = nbasis(p), pt + 1
+        self.Nst = self.N * self.Ng
+
+    def time_matrix(self):
+        K = np.empty((self.Ng, self.Ng))
+        _lib.check(_lib.load().stdg_ref_time_matrix(self._h, K.ctypes.data_as(_lib.DP)))
+        return K
+
+    def eval(self, xi):
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        phi = np.empty((len(xi), self.N)); dphi = np.empty((len(xi), 3, self.N))
+        _lib.check(_lib.load().stdg_ref_eval(self._h, xi.ctypes.data_as(_lib.DP), len(xi),
+                                             phi.ctypes.data_as(_lib.DP), dphi.ctypes.data_as(_lib.DP)))
+        return phi, dphi
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib._lib is not None:
+            _lib._lib.stdg_ref_destroy(self._h)
+            self._h = None
+
+
+def tet_rule(n):
+    """Collapsed Gauss-Jacobi tetrahedron rule of the library (host code)."""
+    xi = np.empty((n ** 3, 3)); w = np.empty(n ** 3)
+    _lib.check(_lib.load().stdg_tet_rule(int(n), xi.ctypes.data_as(_lib.DP), w.ctypes.data_as(_lib.DP)))
+    return xi, w
+
+
+class Solver:
+    """Device-resident discretisation: blocks, state and Krylov workspace (stdg_solver_create)."""
+
+    def __init__(self, mesh: Mesh, ref: Reference, dt, precision="fp64", restart=50, max_iters=200000,
+                 stream=None):
+        torch = _torch()
+        lib = _lib.load()
+        self.mesh, self.ref = mesh, ref
+        self.N, self.Ng, self.Nst = ref.N, ref.Ng, ref.Nst
+        self.ne, self.nf = mesh.ne, mesh.nf
+        self.dt = float(dt)
+        opts = SolverOptions(PREC[precision], int(restart), int(max_iters))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _lib.check(lib.stdg_solver_create(mesh._h, ref._h, self.dt, C.byref(opts),
+                                          C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    # ---------------------------------------------------------------- helpers
+    def pressure_empty(self):
+        torch = _torch()
+        return torch.empty(self.ne * self.Nst, dtype=torch.float64, device="cuda")
+
+    def velocity_empty(self):
+        torch = _torch()
+        return torch.empty(self.nf * 3 * self.Nst, dtype=torch.float64, device="cuda")
+
+    @staticmethod
+    def _dev(t):
+        torch = _torch()
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "expect contiguous cuda float64"
+        return t
+
+    # ---------------------------------------------------------------- hot path
+    def set_dt(self, dt):
+        self.dt = float(dt)
+        _lib.check(_lib.load().stdg_set_dt(self._h, self.dt))
+
+    def pressure_apply(self, x, y=None, pinned=True):
+        x = self._dev(x)
+        y = self.pressure_empty() if y is None else self._dev(y)
+        _lib.check(_lib.load().stdg_pressure_apply(self._h, _ptr(x), _ptr(y), int(bool(pinned))))
+        return y
+
+    def pressure_rhs(self, F, b=None, pinned=True):
+        F = self._dev(F)
+        b = self.pressure_empty() if b is None else self._dev(b)
+        _lib.check(_lib.load().stdg_pressure_rhs(self._h, _ptr(F), _ptr(b), int(bool(pinned))))
+        return b
+
+    def velocity_update(self, F, dp, V=None):
+        F, dp = self._dev(F), self._dev(dp)
+        V = self.velocity_empty() if V is None else self._dev(V)
+        _lib.check(_lib.load().stdg_velocity_update(self._h, _ptr(F), _ptr(dp), _ptr(V)))
+        return V
+
+    def solve(self, b, tol=1e-10, method="kron_cg", x=None):
+        b = self._dev(b)
+        x = self.pressure_empty() if x is None else self._dev(x)
+        st = SolveStats()
+        _lib.check(_lib.load().stdg_solve(self._h, _ptr(b), _ptr(x), float(tol), SOLVER[method], C.byref(st)))
+        return x, {"iterations": st.iterations, "restarts": st.restarts, "rel_residual": st.rel_residual,
+                   "seconds": st.seconds}
+
+    def velocity_moments(self, V, U=None):
+        torch = _torch()
+        V = self._dev(V)
+        U = torch.empty(self.nf * 6 * self.Nst, dtype=torch.float64, device="cuda") if U is None else U
+        _lib.check(_lib.load().stdg_velocity_moments(self._h, _ptr(V), _ptr(U)))
+        return U
+
+    # ---------------------------------------------------------------- time stepping
+    def set_initial(self, field):
+        _lib.check(_lib.load().stdg_set_initial(self._h, C.byref(field)))
+
+    def set_boundary(self, field):
+        _lib.check(_lib.load().stdg_set_boundary(self._h, C.byref(field)))
+
+    def step(self, nu, n_picard, method="kron_cg", tol=1e-10):
+        st = StepStats()
+        _lib.check(_lib.load().stdg_step(self._h, float(nu), int(n_picard), SOLVER[method], float(tol), C.byref(st)))
+        k = st.picard
+        return {"picard": k, "press_iters": list(st.press_iters[:k]), "visc_iters": list(st.visc_iters[:k]),
+                "press_residual": list(st.press_residual[:k]), "seconds": st.seconds,
+                "max_divergence": st.max_divergence}
+
+    def get_state(self):
+        torch = _torch()
+        P, V = self.pressure_empty(), self.velocity_empty()
+        t = C.c_double()
+        _lib.check(_lib.load().stdg_get_state(self._h, _ptr(P), _ptr(V), 1, C.byref(t)))
+        return P, V, t.value
+
+    def set_state(self, P, V, t):
+        _lib.check(_lib.load().stdg_set_state(self._h, _ptr(self._dev(P)), _ptr(self._dev(V)), 1, float(t)))
+
+    def profile(self, enable=True):
+        _lib.check(_lib.load().stdg_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        st = _lib.ProfileStats()
+        _lib.check(_lib.load().stdg_profile_read(self._h, C.byref(st)))
+        return {"kernel_launches": st.kernel_launches, "operator_launches": st.operator_launches,
+                "operator_ms": st.operator_ms}
+
+    def blocks(self):
+        N, nf, ne = self.N, self.nf, self.ne
+        Q = np.empty((nf, 2, 3, N, N)); Mij = np.empty((nf, 2, N, N))
+        A = np.empty((nf, N, N)); B = np.empty((ne, N, N))
+        _lib.check(_lib.load().stdg_get_blocks(self._h, Q.ctypes.data_as(_lib.DP), Mij.ctypes.data_as(_lib.DP),
+                                               A.ctypes.data_as(_lib.DP), B.ctypes.data_as(_lib.DP)))
+        return {"Q": Q, "Mij": Mij, "Aoff": A, "Bdiag": B}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib._lib is not None:
+            _lib._lib.stdg_solver_destroy(self._h)
+            self._h = None

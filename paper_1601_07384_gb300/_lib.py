@@ -1,0 +1,103 @@
+"""ctypes declarations of the C ABI in include/stdg.h (argument marshalling only)."""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstdg.so")
+
+STATUS = {0: "STDG_OK", -1: "STDG_EINVAL", -2: "STDG_ENOMEM", -3: "STDG_ECUDA", -4: "STDG_ENOCONV",
+          -5: "STDG_EMESH", -6: "STDG_ENAN", -7: "STDG_ETIMEOUT", -8: "STDG_EUNSUPPORTED"}
+SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2}
+PREC = {"fp64": 0, "df32": 1}
+FIELD = {"zero": 0, "constant": 1, "beltrami": 2}
+
+
+class StdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("rel_residual", C.c_double),
+                ("seconds", C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("picard", C.c_int), ("press_iters", C.c_int * 8), ("visc_iters", C.c_int * 8),
+                ("press_residual", C.c_double * 8), ("seconds", C.c_double),
+                ("max_divergence", C.c_double)]
+
+
+class SolverOptions(C.Structure):
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int)]
+
+
+class ProfileStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("operator_launches", C.c_int64), ("operator_ms", C.c_double)]
+
+
+class Field(C.Structure):
+    _fields_ = [("kind", C.c_int), ("c", C.c_double * 3), ("a", C.c_double), ("d", C.c_double),
+                ("nu", C.c_double)]
+
+
+P = C.c_void_p
+I64P = C.POINTER(C.c_int64)
+I32P = C.POINTER(C.c_int32)
+DP = C.POINTER(C.c_double)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "stdg_mesh_create": (C.c_int, [DP, C.c_int64, I64P, C.c_int64, C.POINTER(P)]),
+    "stdg_mesh_destroy": (None, [P]),
+    "stdg_mesh_info": (C.c_int, [P, I64P, I64P, I64P, I64P]),
+    "stdg_mesh_faces": (C.c_int, [P, I64P, I64P, I32P, I32P]),
+    "stdg_reference_matrices": (C.c_int, [C.c_int, C.c_int, C.POINTER(P)]),
+    "stdg_ref_destroy": (None, [P]),
+    "stdg_ref_time_matrix": (C.c_int, [P, DP]),
+    "stdg_ref_eval": (C.c_int, [P, DP, C.c_int64, DP, DP]),
+    "stdg_tet_rule": (C.c_int, [C.c_int, DP, DP]),
+    "stdg_solver_create": (C.c_int, [P, P, C.c_double, C.POINTER(SolverOptions), P, C.POINTER(P)]),
+    "stdg_solver_destroy": (None, [P]),
+    "stdg_set_dt": (C.c_int, [P, C.c_double]),
+    "stdg_pressure_apply": (C.c_int, [P, P, P, C.c_int]),
+    "stdg_pressure_rhs": (C.c_int, [P, P, P, C.c_int]),
+    "stdg_velocity_update": (C.c_int, [P, P, P, P]),
+    "stdg_solve": (C.c_int, [P, P, P, C.c_double, C.c_int, C.POINTER(SolveStats)]),
+    "stdg_set_initial": (C.c_int, [P, C.POINTER(Field)]),
+    "stdg_set_boundary": (C.c_int, [P, C.POINTER(Field)]),
+    "stdg_step": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.POINTER(StepStats)]),
+    "stdg_get_state": (C.c_int, [P, P, P, C.c_int, DP]),
+    "stdg_set_state": (C.c_int, [P, P, P, C.c_int, C.c_double]),
+    "stdg_velocity_moments": (C.c_int, [P, P, P]),
+    "stdg_get_blocks": (C.c_int, [P, DP, DP, DP, DP]),
+    "stdg_profile": (C.c_int, [P, C.c_int]),
+    "stdg_profile_read": (C.c_int, [P, C.POINTER(ProfileStats)]),
+    "stdg_last_error": (C.c_char_p, []),
+    "stdg_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libstdg.so (fails loudly: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libstdg.so not built ({path}); run paper_1601_07384_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != 0:
+        msg = _lib.stdg_last_error().decode(errors="replace") if _lib else ""
+        raise StdgError(status, msg)

@@ -1,0 +1,122 @@
+// Device-side declarations shared by the stdg CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+#define STDG_CUDA(call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      stdg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                      __LINE__);                                                         \
+      return STDG_ECUDA;                                                                 \
+    }                                                                                    \
+  } while (0)
+
+#define STDG_LAUNCH_CHECK()                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess) {                                                             \
+      stdg::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),        \
+                      __FILE__, __LINE__);                                               \
+      return STDG_ECUDA;                                                                 \
+    }                                                                                    \
+  } while (0)
+
+namespace stdg {
+
+constexpr int kMaxN = 35;   // p <= 4
+constexpr int kMaxNg = 5;   // p_t <= 4
+
+// Multi-index exponents passed by value to kernels.
+struct MultiIdx { unsigned char e[3 * kMaxN]; };
+
+// Device copies of the mesh.
+struct DevMesh {
+  int ne = 0, nf = 0;
+  int *left = nullptr, *right = nullptr, *fl = nullptr, *fr = nullptr;
+  int *code_l = nullptr, *code_r = nullptr;
+  int *t2f = nullptr, *t2n = nullptr, *t2code = nullptr;
+  double *X0 = nullptr, *J = nullptr, *Jinv = nullptr, *detJ = nullptr, *bary = nullptr;
+  double *fvx = nullptr, *normal = nullptr, *area = nullptr;
+};
+
+// Device copies of the reference tables (layouts as in stdg_ref).
+struct DevRef {
+  double *sub_lin_xi = nullptr, *sub_lin_w = nullptr, *sub_lin_phi = nullptr, *sub_lin_dphi = nullptr;
+  double *tri_lin_st = nullptr, *tri_lin_w = nullptr, *face_lin_phi = nullptr;
+  double *sub_nl_xi = nullptr, *sub_nl_w = nullptr;
+  double *tet_nl_xi = nullptr, *tet_nl_w = nullptr, *tet_nl_phi = nullptr, *tet_nl_dphi = nullptr;
+  double *tri_nl_st = nullptr, *tri_nl_w = nullptr, *face_nl_phi = nullptr;
+};
+
+// Small time matrices passed by value.
+struct TimeMats {
+  double Tp[kMaxNg * kMaxNg];     // dt^2 K^-1
+  double K[kMaxNg * kMaxNg];
+  double Kinv[kMaxNg * kMaxNg];
+  double g0[kMaxNg], g1[kMaxNg];
+};
+
+// Launchers (precompute.cu)
+cudaError_t launch_face_blocks(const DevMesh& m, const DevRef& r, int p, int N, int nq, int nqf,
+                               const MultiIdx& mi, double* Q, double* Mij, double* C, double* x0h,
+                               cudaStream_t st);
+cudaError_t launch_assemble(const DevMesh& m, int N, const double* Q, double* Aoff, double* Bdiag,
+                            double* Bvisc, cudaStream_t st);
+
+}  // namespace stdg
+
+namespace stdg {
+
+// Generic five-point block operator on tets (pressure operator of Eq. CS_19, or the viscous
+// operator of Eq. A1_mod which shares its spatial blocks):
+//   acc_i = (Bdiag_i + extra_coef Bextra_i) x_i + Sum_{f: interior} A_{i,p(i,f)} x_p
+//   y_i[a][k] = scale Sum_b Tacc[a][b] acc_i[b][k] + mass_coef detJ_i Sum_b Kmass[a][b] x_i[b][k]
+// with Tacc = identity when tacc_identity.  pinned: x at (tet 0, mode 0, every a) read as 0,
+// y there = pin_diag * x.
+struct ApplyArgs {
+  int ne, N, Ng;
+  const int *t2f, *t2n, *left;
+  const double *Bdiag, *Aoff, *Bextra, *detJ;
+  double extra_coef, scale, mass_coef, pin_diag;
+  int tacc_identity, pinned;
+  double Tacc[kMaxNg * kMaxNg];
+  double Kmass[kMaxNg * kMaxNg];
+};
+cudaError_t launch_apply(const ApplyArgs& a, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_apply_df32(const ApplyArgs& a, const double* x, double* y, cudaStream_t st);
+
+// b_i[a][l] = coef Sum_{f} Sum_c Sum_m Q^c_{s(i,j)}[m][l] F_j[c][a][m]   (D = -Q^T; coef = -dt)
+cudaError_t launch_rhs(int ne, int N, int Ng, const int* t2f, const int* left, const double* Q,
+                       const double* F, double coef, int pinned, double* b, cudaStream_t st);
+// V_j = F_j - dt (I (x) K^-1) Sum_s Q_sj dp_s on interior faces, V_j = F_j on boundary faces.
+cudaError_t launch_update(int nf, int N, int Ng, const int* left, const int* right, const double* Q,
+                          const double* F, const double* dp, double dt, const double* Kinv,
+                          double* V, cudaStream_t st);
+// U_j[s][c][a][k] = dt Sum_l Mij_s[k][l] V_j[c][a][l]
+cudaError_t launch_moments(int nf, int N, int Ng, const double* Mij, const double* V, double dt,
+                           double* U, cudaStream_t st);
+
+}  // namespace stdg
+
+namespace stdg {
+// Velocity data evaluated on the device (stdg_field).
+struct FieldArg { int kind; double c[3]; double a, d, nu; };
+
+__device__ inline void eval_field(const FieldArg& f, const double* x, double t, double* v) {
+  if (f.kind == STDG_FIELD_CONSTANT) { v[0] = f.c[0]; v[1] = f.c[1]; v[2] = f.c[2]; return; }
+  if (f.kind == STDG_FIELD_BELTRAMI) {
+    const double a = f.a, d = f.d, X = x[0], Y = x[1], Z = x[2];
+    const double e = exp(-f.nu * d * d * t);
+    v[0] = -a * (exp(a * X) * sin(a * Y + d * Z) + exp(a * Z) * cos(a * X + d * Y)) * e;
+    v[1] = -a * (exp(a * Y) * sin(a * Z + d * X) + exp(a * X) * cos(a * Y + d * Z)) * e;
+    v[2] = -a * (exp(a * Z) * sin(a * X + d * Y) + exp(a * Y) * cos(a * Z + d * X)) * e;
+    return;
+  }
+  v[0] = v[1] = v[2] = 0.0;
+}
+}  // namespace stdg

@@ -1,0 +1,476 @@
+// Krylov solvers on the device (Sec. 2.4: matrix-free, unpreconditioned GMRES; Sec. 2.7: CG for
+// p_t = 0).  Every reduction is two-stage over a fixed grid, so results are bitwise
+// reproducible run to run.  Vectors use the pressure layout P[ne][Ng][N].
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solver.h"
+
+namespace stdg {
+
+constexpr int kRedBlocks = 1216;   // 8 x 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kMaxCols = 64;
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce `cnt` per-thread values (cnt <= 8) into part[blockIdx.x * stride + c].
+__device__ inline void block_reduce_store(double* v, int cnt, double* part, int stride) {
+  __shared__ double red[8][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < cnt; ++c) {
+    double s = warp_sum(v[c]);
+    if (lane == 0) red[c][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double s = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) s += red[threadIdx.x][k];
+    part[blockIdx.x * stride + threadIdx.x] = s;
+  }
+}
+
+// per-time-column dot products: part[b][a] = Sum over this block's elements of column a
+__global__ void __launch_bounds__(kRedThreads) k_coldot(int64_t n, int N, int Ng, const double* __restrict__ x,
+                                                       const double* __restrict__ y, double* part) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)((e / N) % Ng);
+    acc[a] = fma(x[e], y[e], acc[a]);
+  }
+  block_reduce_store(acc, Ng, part, Ng);
+}
+
+// x += alpha_a p; r -= alpha_a q; partials of r.r per column (slot a) and of ||(I (x) Tp) r||^2 (slot Ng)
+struct TpArg { double v[kMaxNg * kMaxNg]; };
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t ne, int N, int Ng, const double* __restrict__ alpha,
+                                                          double* __restrict__ x, double* __restrict__ r,
+                                                          const double* __restrict__ p, const double* __restrict__ q,
+                                                          TpArg Tp, double* part) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double al[kMaxNg];
+  for (int a = 0; a < Ng; ++a) al[a] = alpha[a];
+  const int64_t npairs = ne * N;
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npairs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int k = (int)(e % N);
+    double rv[kMaxNg];
+    for (int a = 0; a < Ng; ++a) {
+      const int64_t o = i * Nst + a * N + k;
+      x[o] = fma(al[a], p[o], x[o]);
+      double rn = fma(-al[a], q[o], r[o]);
+      r[o] = rn;
+      rv[a] = rn;
+      acc[a] = fma(rn, rn, acc[a]);
+    }
+    for (int a = 0; a < Ng; ++a) {
+      double w = 0.0;
+      for (int b = 0; b < Ng; ++b) w = fma(Tp.v[a * Ng + b], rv[b], w);
+      acc[Ng] = fma(w, w, acc[Ng]);
+    }
+  }
+  block_reduce_store(acc, Ng + 1, part, Ng + 1);
+}
+
+// p = r + beta_a p
+__global__ void k_cg_dir(int64_t n, int N, int Ng, const double* __restrict__ beta, const double* __restrict__ r,
+                         double* __restrict__ p) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)((e / N) % Ng);
+    p[e] = fma(beta[a], p[e], r[e]);
+  }
+}
+
+// out[c] = Sum_b part[b * width + c] in fixed order (one block per column)
+__global__ void k_final(int nparts, int width, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double red[kRedThreads / 32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * width + c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) t += red[k];
+    out[c] = t;
+  }
+}
+
+// alpha_a = rr_a / pq_a ; (guarded)
+__global__ void k_cg_alpha(int Ng, const double* rr, const double* pq, double* alpha) {
+  int a = threadIdx.x;
+  if (a < Ng) alpha[a] = (pq[a] != 0.0) ? rr[a] / pq[a] : 0.0;
+}
+// beta_a = rrnew_a / rr_a; rr <- rrnew; res = sqrt(tp2)
+__global__ void k_cg_beta(int Ng, double* rr, const double* rrnew, double* beta, double* res) {
+  int a = threadIdx.x;
+  if (a < Ng) {
+    beta[a] = (rr[a] != 0.0) ? rrnew[a] / rr[a] : 0.0;
+    rr[a] = rrnew[a];
+  }
+  if (a == 0) res[0] = sqrt(rrnew[Ng]);
+}
+
+// y_a-mixing: out[i][a][k] = coef Sum_b M[a][b] in[i][b][k]
+__global__ void k_timemix(int64_t ne, int N, int Ng, TpArg M, double coef, const double* __restrict__ in,
+                          double* __restrict__ out) {
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int k = (int)(e % N);
+    double v[kMaxNg];
+    for (int b = 0; b < Ng; ++b) v[b] = in[i * Nst + b * N + k];
+    for (int a = 0; a < Ng; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < Ng; ++b) s = fma(M.v[a * Ng + b], v[b], s);
+      out[i * Nst + a * N + k] = coef * s;
+    }
+  }
+}
+
+// GMRES helpers -------------------------------------------------------------------------------
+// part[v][b]: dot of basis vector v with w over this block's range
+__global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const double* __restrict__ Vb,
+                                                         const double* __restrict__ w, double* part) {
+  const int v = blockIdx.y;
+  const double* vv = Vb + (size_t)v * n;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(vv[e], w[e], acc);
+  __shared__ double red[kRedThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) s += red[k];
+    part[(size_t)blockIdx.x * gridDim.y + v] = s;
+  }
+}
+// w += sign Sum_v h[v] V[v]
+__global__ void k_multiaxpy(int64_t n, int nv, const double* __restrict__ Vb, const double* __restrict__ h,
+                            double sign, double* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int v = 0; v < nv; ++v) s = fma(h[v], Vb[(size_t)v * n + e], s);
+    w[e] = fma(sign, s, w[e]);
+  }
+}
+__global__ void __launch_bounds__(kRedThreads) k_sumsq(int64_t n, const double* __restrict__ x, double* part) {
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[e], x[e], acc);
+  block_reduce_store(&acc, 1, part, 1);
+}
+__global__ void k_scale_copy(int64_t n, const double* __restrict__ in, const double* __restrict__ sc, int mode,
+                             double* __restrict__ out) {
+  // mode 0: out = in / sqrt(sc[0]);  mode 1: out = in - out (residual r = b - Ax, out holds Ax)
+  double f = (mode == 0) ? 1.0 / sqrt(sc[0]) : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (mode == 0) ? in[e] * f : in[e] - out[e];
+}
+
+stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return STDG_ENOMEM;
+  }
+  s->allocs.push_back(*p);
+  return STDG_OK;
+}
+
+stdg_status ensure_krylov(stdg_solver* s) {
+  if (s->kb) return STDG_OK;
+  const size_t n = (size_t)s->ne * s->Nst * sizeof(double);
+  stdg_status st;
+  for (double** v : {&s->kb, &s->kx, &s->kr, &s->kp, &s->kq})
+    if ((st = dev_alloc(s, (void**)v, n)) != STDG_OK) return st;
+  if ((st = dev_alloc(s, (void**)&s->part, (size_t)kRedBlocks * kMaxCols * sizeof(double))) != STDG_OK) return st;
+  if ((st = dev_alloc(s, (void**)&s->scal, 1024 * sizeof(double))) != STDG_OK) return st;
+  if (cudaMallocHost((void**)&s->hostbuf, 1024 * sizeof(double)) != cudaSuccess) {
+    set_error("cudaMallocHost failed");
+    return STDG_ENOMEM;
+  }
+  return STDG_OK;
+}
+
+static stdg_status ensure_basis(stdg_solver* s, int cols) {
+  if (s->basis && s->basis_cols >= cols) return STDG_OK;
+  const size_t n = (size_t)s->ne * s->Nst;
+  return dev_alloc(s, (void**)&s->basis, (size_t)cols * n * sizeof(double)) == STDG_OK
+             ? (s->basis_cols = cols, STDG_OK)
+             : STDG_ENOMEM;
+}
+
+static double host_norm(stdg_solver* s, const double* v, int64_t n) {
+  ++s->nlaunch;
+  k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, v, s->part);
+  ++s->nlaunch;
+  k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, s->part, s->scal + 900);
+  cudaMemcpyAsync(s->hostbuf + 900, s->scal + 900, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  cudaStreamSynchronize(s->stream);
+  return std::sqrt(s->hostbuf[900]);
+}
+
+void prof_fold(stdg_solver* s) {
+  if (s->ev_used == 0) return;
+  cudaEventSynchronize(s->ev[2 * s->ev_used - 1]);
+  for (int k = 0; k < s->ev_used; ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]);
+    s->op_ms += ms;
+  }
+  s->ev_used = 0;
+}
+
+static stdg_status op_apply(stdg_solver* s, const ApplyArgs& a, const double* x, double* y) {
+  const bool prof = s->prof && !s->ev.empty();
+  if (prof) {
+    if (2 * s->ev_used >= (int)s->ev.size()) prof_fold(s);
+    cudaEventRecord(s->ev[2 * s->ev_used], s->stream);
+  }
+  ++s->nlaunch;
+  ++s->op_launches;
+  cudaError_t e = (s->opt.precision == STDG_PREC_DF32 && s->blk32 && a.Bextra == nullptr)
+                      ? launch_apply_df32(a, x, y, s->stream)
+                      : launch_apply(a, x, y, s->stream);
+  if (prof) {
+    cudaEventRecord(s->ev[2 * s->ev_used + 1], s->stream);
+    ++s->ev_used;
+  }
+  if (e != cudaSuccess) { set_error("operator launch failed: %s", cudaGetErrorString(e)); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+static ApplyArgs pressure_op(stdg_solver* s, int pinned, int kron, double scale, double pin_diag) {
+  ApplyArgs a{};
+  a.ne = (int)s->ne; a.N = s->N; a.Ng = s->Ng;
+  a.t2f = s->dm.t2f; a.t2n = s->dm.t2n; a.left = s->dm.left;
+  a.Bdiag = s->Bdiag; a.Aoff = s->Aoff; a.Bextra = nullptr; a.detJ = s->dm.detJ;
+  a.extra_coef = 0.0; a.scale = scale; a.mass_coef = 0.0; a.pin_diag = pin_diag;
+  a.tacc_identity = kron; a.pinned = pinned;
+  for (int q = 0; q < s->Ng * s->Ng; ++q) a.Tacc[q] = s->tm.Tp[q];
+  return a;
+}
+
+stdg_status apply_pressure(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
+                           double pin_diag) {
+  return op_apply(s, pressure_op(s, pinned, kron, scale, pin_diag), x, y);
+}
+
+// Block CG for an operator that is symmetric positive definite on each time column.
+// x holds the initial guess unless zero_x0.  Stops when ||(I (x) mix) r|| <= tol_abs.
+static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* rhs, double* x, bool zero_x0,
+                            const TpArg& mix, double tol_abs, int* iters, double* res_abs) {
+  const int N = s->N, Ng = s->Ng;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  double* r = s->kr; double* p = s->kp; double* q = s->kq;
+  double* rr = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
+  double* rrnew = s->scal + 32; double* res = s->scal + 48;
+  if (zero_x0) {
+    cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+    cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  } else {
+    stdg_status e = op_apply(s, op, x, r);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, rhs, nullptr, 1, r);
+  }
+  cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  ++s->nlaunch;
+  k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, r, s->part);
+  ++s->nlaunch;
+  k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rr);
+  int it = 0;
+  double rabs = INFINITY;
+  const int maxit = s->opt.max_iters;
+  while (it < maxit) {
+    stdg_status e = op_apply(s, op, p, q);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
+    ++s->nlaunch;
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
+    ++s->nlaunch;
+    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rr, pq, alpha);
+    ++s->nlaunch;
+    k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part);
+    ++s->nlaunch;
+    k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
+    ++s->nlaunch;
+    k_cg_beta<<<1, 32, 0, s->stream>>>(Ng, rr, rrnew, beta, res);
+    ++s->nlaunch;
+    k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, r, p);
+    cudaMemcpyAsync(s->hostbuf, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    ++it;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+    rabs = s->hostbuf[0];
+    if (!std::isfinite(rabs)) { set_error("CG: non-finite residual"); return STDG_ENAN; }
+    if (rabs <= tol_abs) break;
+  }
+  *iters = it;
+  *res_abs = rabs;
+  if (rabs > tol_abs) { set_error("CG reached max_iters (%d)", it); return STDG_ENOCONV; }
+  return STDG_OK;
+}
+
+// Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations on the host.
+// x holds the initial guess unless zero_x0.  Stops when ||b - A x|| <= tol_abs.
+static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
+                         double tol_abs, int* iters, int* nrestarts, double* res_abs) {
+  const int m = s->opt.restart;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  stdg_status e = ensure_basis(s, m + 1);
+  if (e != STDG_OK) return e;
+  if (zero_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double* hd = s->scal + 100;     // h (pass 1) at [0..m], h (pass 2) at [128..], norm^2 at [256]
+  int it = 0, restarts = 0;
+  double beta = INFINITY;
+  const int maxit = s->opt.max_iters;
+  while (true) {
+    e = op_apply(s, op, x, s->kq);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);
+    beta = host_norm(s, s->kq, n);
+    if (!std::isfinite(beta)) { set_error("GMRES: non-finite residual"); return STDG_ENAN; }
+    if (beta <= tol_abs || it >= maxit) break;
+    s->hostbuf[901] = beta * beta;
+    cudaMemcpyAsync(s->scal + 901, s->hostbuf + 901, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, s->kq, s->scal + 901, 0, s->basis);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (k = 0; k < m; ++k) {
+      double* w = s->basis + (size_t)(k + 1) * n;
+      e = op_apply(s, op, s->basis + (size_t)k * n, w);
+      if (e != STDG_OK) return e;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = hd + pass * 128;
+        ++s->nlaunch;
+        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part);
+        ++s->nlaunch;
+        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp);
+        ++s->nlaunch;
+        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w);
+      }
+      ++s->nlaunch;
+      k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
+      ++s->nlaunch;
+      k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, s->part, hd + 256);
+      ++s->nlaunch;
+      k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, hd + 256, 0, w);
+      cudaMemcpyAsync(s->hostbuf, hd, 257 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("GMRES: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = s->hostbuf[i] + s->hostbuf[128 + i];
+      H[(size_t)(k + 1) * m + k] = std::sqrt(s->hostbuf[256]);
+      for (int i = 0; i < k; ++i) {
+        double t1 = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)(i + 1) * m + k] = -sn[i] * H[(size_t)i * m + k] + cs[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = t1;
+      }
+      double den = std::hypot(H[(size_t)k * m + k], H[(size_t)(k + 1) * m + k]);
+      cs[k] = H[(size_t)k * m + k] / den;
+      sn[k] = H[(size_t)(k + 1) * m + k] / den;
+      H[(size_t)k * m + k] = den;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++it;
+      if (!std::isfinite(g[k + 1])) { set_error("GMRES: non-finite residual estimate"); return STDG_ENAN; }
+      if (std::fabs(g[k + 1]) <= tol_abs || it >= maxit) { ++k; break; }
+    }
+    if (k > m) k = m;
+    for (int i = k - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int jj = i + 1; jj < k; ++jj) sum -= H[(size_t)i * m + jj] * y[jj];
+      y[i] = sum / H[(size_t)i * m + i];
+    }
+    std::memcpy(s->hostbuf, y.data(), k * sizeof(double));
+    cudaMemcpyAsync(hd, s->hostbuf, k * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    ++s->nlaunch;
+    k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k, s->basis, hd, 1.0, x);
+    ++restarts;
+  }
+  *iters = it; *nrestarts = restarts; *res_abs = beta;
+  if (beta > tol_abs) { set_error("GMRES reached max_iters (%d)", it); return STDG_ENOCONV; }
+  return STDG_OK;
+}
+
+stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double tol, int method,
+                           stdg_solve_stats* st) {
+  stdg_status e = ensure_krylov(s);
+  if (e != STDG_OK) return e;
+  auto t0 = std::chrono::steady_clock::now();
+  if (method == STDG_SOLVER_CG && s->pt != 0) {
+    set_error("STDG_SOLVER_CG needs p_t = 0 (the system is nonsymmetric otherwise)");
+    return STDG_EINVAL;
+  }
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  const double bn = host_norm(s, b, n);
+  int it = 0, rs = 0;
+  double rabs = 0.0;
+  stdg_status r = STDG_OK;
+  if (bn == 0.0) {
+    cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+  } else if (method == STDG_SOLVER_GMRES) {
+    r = gmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it, &rs, &rabs);
+  } else if (method == STDG_SOLVER_CG || method == STDG_SOLVER_KRON_CG) {
+    // A = A_sp (x) Tp (pinned):  A x = b  <=>  (-A_sp (x) I) x = -(I (x) Tp^-1) b,  Tp^-1 = K / dt^2;
+    // the full residual is b - A x = -(I (x) Tp) r for the CG residual r.
+    TpArg Tp{}, Tpinv{};
+    const double idt2 = 1.0 / (s->dt * s->dt);
+    for (int q = 0; q < s->Ng * s->Ng; ++q) { Tp.v[q] = s->tm.Tp[q]; Tpinv.v[q] = s->tm.K[q] * idt2; }
+    ++s->nlaunch;
+    k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, s->N, s->Ng, Tpinv, -1.0, b, s->kb);
+    r = cg_block(s, pressure_op(s, 1, 1, -1.0, 1.0), s->kb, x, true, Tp, tol * bn, &it, &rabs);
+  } else {
+    set_error("unknown solver method %d", method);
+    return STDG_EINVAL;
+  }
+  if (r != STDG_OK && r != STDG_ENOCONV) return r;
+  if (st) {
+    // report the residual of the full pinned system for every method
+    stdg_status e2 = apply_pressure(s, x, s->kq, 1, 0, 1.0, -1.0);
+    if (e2 != STDG_OK) return e2;
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);
+    st->iterations = it;
+    st->restarts = rs;
+    st->rel_residual = bn > 0 ? host_norm(s, s->kq, n) / bn : 0.0;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return r;
+}
+
+stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
+                          double* res) {
+  ApplyArgs a{};
+  a.ne = (int)s->ne; a.N = s->N; a.Ng = s->Ng;
+  a.t2f = s->dm.t2f; a.t2n = s->dm.t2n; a.left = s->dm.left;
+  a.Bdiag = s->Bdiag; a.Aoff = s->Aoff; a.Bextra = s->Bvisc; a.detJ = s->dm.detJ;
+  a.extra_coef = -1.0; a.scale = -nu * s->dt; a.mass_coef = 1.0; a.pin_diag = 0.0;
+  a.tacc_identity = 1; a.pinned = 0;
+  for (int q = 0; q < s->Ng * s->Ng; ++q) a.Kmass[q] = s->K[q];
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  const double bn = host_norm(s, b, n);
+  if (bn == 0.0) { cudaMemsetAsync(x, 0, n * sizeof(double), s->stream); *iters = 0; *res = 0; return STDG_OK; }
+  int rs = 0;
+  if (s->pt == 0) {
+    TpArg I{};
+    I.v[0] = 1.0;
+    return cg_block(s, a, b, x, false, I, tol * bn, iters, res);
+  }
+  return gmres(s, a, b, x, false, tol * bn, iters, &rs, res);
+}
+
+}  // namespace stdg

@@ -1,0 +1,619 @@
+// Support steps of the Picard pressure-correction algorithm (Sec. 2.5-2.6) and its driver.
+// Main-grid velocity is stored component-major, Vbar[c][ne][Ng][N], so that each component is a
+// pressure-layout vector for the viscous solves.  With orthonormal bases (M_i = dt |J_i| I,
+// M_{i,j} = dt M^sp_ij, Mbar_j = dt I, M_j = I (x) K, Mbar_i = |J_i| I (x) K):
+//   average   vbar_i   = |J_i|^-1 Sum_{j in S_i} M^sp_ij v_j                     (Eq. average)
+//   prevpress Lambda_i = |J_i|^-1 Sum_{j in S_i} M^sp_ij g_j,
+//             g_j = dt (I (x) K^-1) Sum_s Q^sp_sj p_s  (boundary: volume part only)  (Eq. prevpress)
+//   convection Upsilon^c_i (Eq. convdg, Rusanov flux, s_max = 2 max(|v+|, |v-|) pointwise)
+//   goback    F_j = Sum_s M^sp_sj^T vbar_s                                       (Eq. goback)
+//   viscous   |J_i| K-mixing + nu dt (-(A_sp x)_i + Bvisc_i x_i) = rhs          (Eq. A1_mod)
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solver.h"
+
+namespace stdg {
+
+struct GArg { double v[kMaxNg]; };
+struct MArg { double v[kMaxNg * kMaxNg]; };
+
+// |det(B - A, C - A, c - A)| = 6 vol(T_ij) for face vertices fv = (A, B, C) and apex c
+__device__ inline double subvol6(const double* fv, const double* c) {
+  double e[3][3];
+  for (int d = 0; d < 3; ++d) { e[0][d] = fv[3 + d] - fv[d]; e[1][d] = fv[6 + d] - fv[d]; e[2][d] = c[d] - fv[d]; }
+  return fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+              e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]));
+}
+
+__device__ inline void psi_hat(int N, const MultiIdx& mi, const double* C, const double* x0h, const double* x,
+                               double* T, double* out) {
+  const double hinv = 1.0 / x0h[3];
+  const double y0 = (x[0] - x0h[0]) * hinv, y1 = (x[1] - x0h[1]) * hinv, y2 = (x[2] - x0h[2]) * hinv;
+  for (int m = 0; m < N; ++m) {
+    double v = 1.0;
+    for (int e = 0; e < mi.e[3 * m]; ++e) v *= y0;
+    for (int e = 0; e < mi.e[3 * m + 1]; ++e) v *= y1;
+    for (int e = 0; e < mi.e[3 * m + 2]; ++e) v *= y2;
+    T[m] = v;
+  }
+  for (int m = 0; m < N; ++m) {
+    double s = 0.0;
+    for (int n = 0; n <= m; ++n) s = fma(C[m * N + n], T[n], s);
+    out[m] = s;
+  }
+}
+
+// ---- averaging: out[c][i][a][k] = 1/|J_i| Sum_f Sum_l Mij[j][s][k][l] in[j][c][a][l]
+__global__ void k_average(int ne, int N, int Ng, const int* __restrict__ t2f, const int* __restrict__ left,
+                          const double* __restrict__ detJ, const double* __restrict__ Mij,
+                          const double* __restrict__ in, double* __restrict__ out) {
+  const int i = blockIdx.x, Nst = N * Ng;
+  const size_t NN = (size_t)N * N;
+  const double inv = 1.0 / detJ[i];
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    const int c = o / Nst, rem = o % Nst, a = rem / N, k = rem % N;
+    double s = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      const int j = t2f[4 * i + f];
+      const int sd = left[j] == i ? 0 : 1;
+      const double* M = Mij + ((size_t)j * 2 + sd) * NN + (size_t)k * N;
+      const double* v = in + ((size_t)j * 3 + c) * Nst + a * N;
+      for (int l = 0; l < N; ++l) s = fma(M[l], v[l], s);
+    }
+    out[((size_t)c * ne + i) * Nst + rem] = s * inv;
+  }
+}
+
+// ---- g_j = dt (I (x) K^-1) Sum_s Q_sj p_s  (boundary: Q volume part of the single side)
+__global__ void k_face_grad(int N, int Ng, const int* __restrict__ left, const int* __restrict__ right,
+                            const double* __restrict__ Q, const double* __restrict__ Pp, double dt, MArg Ki,
+                            double* __restrict__ G) {
+  extern __shared__ double sm[];
+  const int j = blockIdx.x, Nst = N * Ng;
+  const size_t NN = (size_t)N * N;
+  const int l = left[j], r = right[j];
+  double* g = sm;   // 3 x Nst
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    const int c = o / Nst, rem = o % Nst, b = rem / N, m = rem % N;
+    double s = 0.0;
+    if (r >= 0) {
+      for (int sd = 0; sd < 2; ++sd) {
+        const double* q = Q + ((size_t)j * 6 + sd * 3 + c) * NN + (size_t)m * N;
+        const double* pp = Pp + (size_t)(sd ? r : l) * Nst + b * N;
+        for (int ll = 0; ll < N; ++ll) s = fma(q[ll], pp[ll], s);
+      }
+    } else {
+      const double* q = Q + ((size_t)j * 6 + 3 + c) * NN + (size_t)m * N;
+      const double* pp = Pp + (size_t)l * Nst + b * N;
+      for (int ll = 0; ll < N; ++ll) s = fma(q[ll], pp[ll], s);
+    }
+    g[o] = s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    const int c = o / Nst, rem = o % Nst, a = rem / N, m = rem % N;
+    double s = 0.0;
+    for (int b = 0; b < Ng; ++b) s = fma(Ki.v[a * Ng + b], g[c * Nst + b * N + m], s);
+    G[(size_t)j * 3 * Nst + o] = dt * s;
+  }
+}
+
+// ---- goback: F[j][c][a][m] = Sum_s Sum_k Mij[j][s][k][m] vbar[c][s][a][k]; boundary: F = Vbc
+__global__ void k_goback(int ne, int N, int Ng, const int* __restrict__ left, const int* __restrict__ right,
+                         const double* __restrict__ Mij, const double* __restrict__ vbar,
+                         const double* __restrict__ Vbc, double* __restrict__ F) {
+  const int j = blockIdx.x, Nst = N * Ng;
+  const size_t NN = (size_t)N * N;
+  const int l = left[j], r = right[j];
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    if (r < 0) { F[(size_t)j * 3 * Nst + o] = Vbc[(size_t)j * 3 * Nst + o]; continue; }
+    const int c = o / Nst, rem = o % Nst, a = rem / N, m = rem % N;
+    double s = 0.0;
+    for (int sd = 0; sd < 2; ++sd) {
+      const double* M = Mij + ((size_t)j * 2 + sd) * NN + m;
+      const double* v = vbar + ((size_t)c * ne + (sd ? r : l)) * Nst + a * N;
+      for (int k = 0; k < N; ++k) s = fma(M[(size_t)k * N], v[k], s);
+    }
+    F[(size_t)j * 3 * Nst + o] = s;
+  }
+}
+
+// ---- start of a step: V[j][c][0][m] = Sum_a g1[a] Vn[j][c][a][m], other modes 0; boundary = Vbc
+__global__ void k_trace(int nf, int N, int Ng, const int* __restrict__ right, GArg g1, const double* __restrict__ Vn,
+                        const double* __restrict__ Vbc, double* __restrict__ V) {
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nf * 3 * Nst; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / (3 * Nst);
+    const int rem = (int)(e % Nst), a = rem / N, m = rem % N;
+    const int64_t base = e - rem;
+    if (right[j] < 0) { V[e] = Vbc[e]; continue; }
+    if (a != 0) { V[e] = 0.0; continue; }
+    double s = 0.0;
+    for (int b = 0; b < Ng; ++b) s = fma(g1.v[b], Vn[base + b * N + m], s);
+    V[e] = s;
+  }
+}
+
+// ---- viscous right-hand side (Eq. A1_mod):
+// rhs[c][i][a][k] = |J| g0[a] Sum_b g1[b] vbar_n[c][i][b][k] - Ups[c][i][a][k] - |J| Sum_b K[a][b] Lam[c][i][b][k]
+//                   - nu Sum_{boundary f} Sum_d Sum_m Q^{bd,d}[m][k] G[j][c][d][a][m]
+__global__ void k_visc_rhs(int ne, int N, int Ng, const int* __restrict__ t2f, const int* __restrict__ t2n,
+                           const double* __restrict__ detJ, const double* __restrict__ Q, GArg g0, GArg g1, MArg K,
+                           double nu, const double* __restrict__ vbar_n, const double* __restrict__ Ups,
+                           const double* __restrict__ Lam, const double* __restrict__ Gbc, double* __restrict__ rhs) {
+  const int i = blockIdx.x, Nst = N * Ng;
+  const size_t NN = (size_t)N * N;
+  const double dj = detJ[i];
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    const int c = o / Nst, rem = o % Nst, a = rem / N, k = rem % N;
+    const size_t vb = ((size_t)c * ne + i) * Nst;
+    double tr = 0.0, kl = 0.0;
+    for (int b = 0; b < Ng; ++b) {
+      tr = fma(g1.v[b], vbar_n[vb + b * N + k], tr);
+      kl = fma(K.v[a * Ng + b], Lam[vb + b * N + k], kl);
+    }
+    double s = dj * g0.v[a] * tr - Ups[vb + rem] - dj * kl;
+    for (int f = 0; f < 4; ++f) {
+      if (t2n[4 * i + f] >= 0) continue;
+      const int j = t2f[4 * i + f];
+      double bsum = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double* q = Q + ((size_t)j * 6 + d) * NN + k;
+        const double* gg = Gbc + (((size_t)j * 3 + c) * 3 + d) * Nst + a * N;
+        for (int m = 0; m < N; ++m) bsum = fma(q[(size_t)m * N], gg[m], bsum);
+      }
+      s -= nu * bsum;
+    }
+    rhs[vb + rem] = s;
+  }
+}
+
+// ---- boundary data on boundary dual cells T_ij x slab (reading R2 / R25)
+// Vbc[j][c][a][m] = Sum_{q,t} w ψ_m γ_a(τ_t) v_c ; Gbc[j][c][d][a][m] = dt Sum_{qf,t} wf ψ_m γ_a v_c n_d
+__global__ void __launch_bounds__(128) k_boundary(int N, int Ng, int nq, int nqf, int nt, const int* __restrict__ left,
+                                                  const int* __restrict__ right, const int* __restrict__ fl,
+                                                  const double* __restrict__ bary, const double* __restrict__ J,
+                                                  const double* __restrict__ detJ, const double* __restrict__ fvx,
+                                                  const double* __restrict__ normal, const double* __restrict__ area,
+                                                  const double* __restrict__ C, const double* __restrict__ x0h,
+                                                  const double* __restrict__ sub_xi, const double* __restrict__ sub_w,
+                                                  const double* __restrict__ tri_st, const double* __restrict__ tri_w,
+                                                  const double* __restrict__ ttau, const double* __restrict__ tw,
+                                                  const double* __restrict__ tg, MultiIdx mi, FieldArg fld, double t0,
+                                                  double dt, double* __restrict__ Vbc, double* __restrict__ Gbc) {
+  const int j = blockIdx.x;
+  if (right[j] >= 0) return;
+  extern __shared__ double sm[];
+  const int Nst = N * Ng;
+  const int CH = 64;
+  double* ps = sm;                 // CH x N  (w * psi)
+  double* vv = ps + CH * N;        // CH x 3
+  double* tmp = vv + CH * 3;       // CH x N scratch
+  __shared__ int tq[64], tt[64];
+  const int i = left[j];
+  const double* Cj = C + (size_t)j * N * N;
+  const double* xh = x0h + 4 * (size_t)j;
+  const double* fv = fvx + 9 * (size_t)j;
+  const double* nj = normal + 3 * (size_t)j;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int npts = (pass == 0 ? nq : nqf) * nt;
+    for (int base = 0; base < npts; base += CH) {
+      const int cnt = min(CH, npts - base);
+      for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+        const int pt = base + u, q = pt / nt, ti = pt % nt;
+        double x[3], w;
+        if (pass == 0) {
+          // unit-tet rule laid on (A, B, C, barycentre of T_i): the canonical vertex order of T_ij
+          const double* xi = sub_xi + 3 * (size_t)q;
+          const double* bc = bary + 3 * (size_t)i;
+          for (int d = 0; d < 3; ++d)
+            x[d] = fv[d] + xi[0] * (fv[3 + d] - fv[d]) + xi[1] * (fv[6 + d] - fv[d]) + xi[2] * (bc[d] - fv[d]);
+          w = subvol6(fv, bc) * sub_w[q] * tw[ti];
+        } else {
+          const double s = tri_st[2 * q], tt2 = tri_st[2 * q + 1];
+          for (int d = 0; d < 3; ++d) x[d] = fv[d] + s * (fv[3 + d] - fv[d]) + tt2 * (fv[6 + d] - fv[d]);
+          w = 2.0 * area[j] * tri_w[q] * tw[ti] * dt;
+        }
+        psi_hat(N, mi, Cj, xh, x, tmp + u * N, ps + u * N);
+        for (int m = 0; m < N; ++m) ps[u * N + m] *= w;
+        eval_field(fld, x, t0 + ttau[ti] * dt, vv + 3 * u);
+        tq[u] = q; tt[u] = ti;
+      }
+      __syncthreads();
+      const int nout = pass == 0 ? 3 * Nst : 9 * Nst;
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        int c, dd = 0, rem;
+        if (pass == 0) { c = o / Nst; rem = o % Nst; } else { c = o / (3 * Nst); dd = (o / Nst) % 3; rem = o % Nst; }
+        const int a = rem / N, m = rem % N;
+        double s = 0.0;
+        for (int u = 0; u < cnt; ++u) s = fma(ps[u * N + m] * tg[tt[u] * Ng + a], vv[3 * u + c], s);
+        if (pass == 0) {
+          double* dst = Vbc + (size_t)j * 3 * Nst + o;
+          *dst = (base == 0 ? 0.0 : *dst) + s;
+        } else {
+          double* dst = Gbc + (size_t)j * 9 * Nst + o;
+          *dst = (base == 0 ? 0.0 : *dst) + s * nj[dd];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---- initial data: V[j][c][0][m] = Sum_{sides} Sum_q w psi_m v0_c(x_q), other time modes 0
+__global__ void __launch_bounds__(128) k_initial(int N, int Ng, int nq, const int* __restrict__ left,
+                                                 const int* __restrict__ right, const double* __restrict__ fvx,
+                                                 const double* __restrict__ bary,
+                                                 const double* __restrict__ C, const double* __restrict__ x0h,
+                                                 const double* __restrict__ sub_xi, const double* __restrict__ sub_w,
+                                                 MultiIdx mi, FieldArg fld, double* __restrict__ V) {
+  extern __shared__ double sm[];
+  const int j = blockIdx.x, Nst = N * Ng;
+  const int CH = 64;
+  double* ps = sm;
+  double* vv = ps + CH * N;
+  double* tmp = vv + CH * 3;
+  const double* Cj = C + (size_t)j * N * N;
+  const double* xh = x0h + 4 * (size_t)j;
+  const int nsides = right[j] >= 0 ? 2 : 1;
+  const int npts = nq * nsides;
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) V[(size_t)j * 3 * Nst + o] = 0.0;
+  __syncthreads();
+  for (int base = 0; base < npts; base += CH) {
+    const int cnt = min(CH, npts - base);
+    for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+      const int pt = base + u, sd = pt / nq, q = pt % nq;
+      const int i = sd ? right[j] : left[j];
+      const double* xi = sub_xi + 3 * (size_t)q;
+      const double* fv = fvx + 9 * (size_t)j;
+      const double* bc = bary + 3 * (size_t)i;
+      double x[3];
+      for (int d = 0; d < 3; ++d)
+        x[d] = fv[d] + xi[0] * (fv[3 + d] - fv[d]) + xi[1] * (fv[6 + d] - fv[d]) + xi[2] * (bc[d] - fv[d]);
+      const double w = subvol6(fv, bc) * sub_w[q];
+      psi_hat(N, mi, Cj, xh, x, tmp + u * N, ps + u * N);
+      for (int m = 0; m < N; ++m) ps[u * N + m] *= w;
+      eval_field(fld, x, 0.0, vv + 3 * u);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < 3 * N; o += blockDim.x) {
+      const int c = o / N, m = o % N;
+      double s = 0.0;
+      for (int u = 0; u < cnt; ++u) s = fma(ps[u * N + m], vv[3 * u + c], s);
+      V[(size_t)j * 3 * Nst + c * Nst + m] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- Rusanov space-time DG convection on the main grid (Eq. convdg), per tet.
+struct ConvArgs {
+  int ne, N, Ng, nq, nqf, nt;
+  const int *t2f, *t2n, *t2code, *left, *code_l, *code_r;
+  const double *detJ, *Jinv, *normal, *area, *fvx;
+  const double *phi, *dphi, *w, *fphi, *tri_st, *tri_w, *ttau, *tw, *tg;
+  FieldArg fld;
+  double t0, dt;
+  const double* vbar;   // [3][ne][Nst]
+  double* ups;          // [3][ne][Nst]
+};
+
+__global__ void __launch_bounds__(128) k_convection(ConvArgs a) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x, N = a.N, Ng = a.Ng, Nst = N * Ng, ne = a.ne;
+  const int CH = 64;
+  double* acc = sm;                      // 3 x Nst
+  double* Vi = acc + 3 * Nst;            // 3 x Nst (own coefficients)
+  double* Vn = Vi + 3 * Nst;             // 3 x Nst (neighbour coefficients)
+  double* H = Vn + 3 * Nst;              // CH x 9 (volume) or CH x 3 (face)
+  __shared__ int pq[64], pt[64];
+  const double* Ji = a.Jinv + 9 * (size_t)i;
+  const double dj = a.detJ[i];
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    acc[o] = 0.0;
+    const int c = o / Nst, rem = o % Nst;
+    Vi[o] = a.vbar[((size_t)c * ne + i) * Nst + rem];
+  }
+  __syncthreads();
+  // volume term: - int grad(phi~_k) . F_c(vbar)
+  const int nv = a.nq * a.nt;
+  for (int base = 0; base < nv; base += CH) {
+    const int cnt = min(CH, nv - base);
+    for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+      const int p0 = base + u, q = p0 / a.nt, ti = p0 % a.nt;
+      double v[3];
+      for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (int b = 0; b < Ng; ++b) {
+          double sb = 0.0;
+          for (int k = 0; k < N; ++k) sb = fma(a.phi[(size_t)q * N + k], Vi[c * Nst + b * N + k], sb);
+          s = fma(a.tg[ti * Ng + b], sb, s);
+        }
+        v[c] = s;
+      }
+      const double W = a.dt * a.tw[ti] * dj * a.w[q];
+      // H[c][e] = W Sum_d Jinv[e][d] v_c v_d  (grad_x phi_d = Sum_e Jinv[e][d] d_e phi)
+      for (int c = 0; c < 3; ++c)
+        for (int e = 0; e < 3; ++e)
+          H[u * 9 + c * 3 + e] = W * v[c] * (Ji[3 * e] * v[0] + Ji[3 * e + 1] * v[1] + Ji[3 * e + 2] * v[2]);
+      pq[u] = q; pt[u] = ti;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+      const int c = o / Nst, rem = o % Nst, ta = rem / N, k = rem % N;
+      double s = 0.0;
+      for (int u = 0; u < cnt; ++u) {
+        const double* dp = a.dphi + (size_t)pq[u] * 3 * N + k;
+        const double g = a.tg[pt[u] * Ng + ta];
+        s = fma(g, H[u * 9 + c * 3] * dp[0] + H[u * 9 + c * 3 + 1] * dp[N] + H[u * 9 + c * 3 + 2] * dp[2 * N], s);
+      }
+      acc[o] -= s;
+    }
+    __syncthreads();
+  }
+  // face terms: + int_{face} phi~_k F^RS . n_i
+  for (int f = 0; f < 4; ++f) {
+    const int j = a.t2f[4 * i + f];
+    const int nb = a.t2n[4 * i + f];
+    const bool me_left = a.left[j] == i;
+    const int code = a.t2code[4 * i + f];
+    const int codeb = nb >= 0 ? (me_left ? a.code_r[j] : a.code_l[j]) : 0;
+    const double sg = me_left ? 1.0 : -1.0;
+    const double n0 = sg * a.normal[3 * j], n1 = sg * a.normal[3 * j + 1], n2 = sg * a.normal[3 * j + 2];
+    const double* fv = a.fvx + 9 * (size_t)j;
+    if (nb >= 0) {
+      for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+        const int c = o / Nst, rem = o % Nst;
+        Vn[o] = a.vbar[((size_t)c * ne + nb) * Nst + rem];
+      }
+    }
+    __syncthreads();
+    const int nfp = a.nqf * a.nt;
+    for (int base = 0; base < nfp; base += CH) {
+      const int cnt = min(CH, nfp - base);
+      for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+        const int p0 = base + u, q = p0 / a.nt, ti = p0 % a.nt;
+        double vm[3], vp[3];
+        const double* ph = a.fphi + ((size_t)code * a.nqf + q) * N;
+        for (int c = 0; c < 3; ++c) {
+          double s = 0.0;
+          for (int b = 0; b < Ng; ++b) {
+            double sb = 0.0;
+            for (int k = 0; k < N; ++k) sb = fma(ph[k], Vi[c * Nst + b * N + k], sb);
+            s = fma(a.tg[ti * Ng + b], sb, s);
+          }
+          vm[c] = s;
+        }
+        if (nb >= 0) {
+          const double* phn = a.fphi + ((size_t)codeb * a.nqf + q) * N;
+          for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int b = 0; b < Ng; ++b) {
+              double sb = 0.0;
+              for (int k = 0; k < N; ++k) sb = fma(phn[k], Vn[c * Nst + b * N + k], sb);
+              s = fma(a.tg[ti * Ng + b], sb, s);
+            }
+            vp[c] = s;
+          }
+        } else {
+          const double s = a.tri_st[2 * q], t = a.tri_st[2 * q + 1];
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = fv[d] + s * (fv[3 + d] - fv[d]) + t * (fv[6 + d] - fv[d]);
+          eval_field(a.fld, x, a.t0 + a.ttau[ti] * a.dt, vp);
+        }
+        const double unm = vm[0] * n0 + vm[1] * n1 + vm[2] * n2;
+        const double unp = vp[0] * n0 + vp[1] * n1 + vp[2] * n2;
+        const double smax = 2.0 * fmax(sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]),
+                                       sqrt(vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]));
+        const double W = a.dt * a.tw[ti] * 2.0 * a.area[j] * a.tri_w[q];
+        for (int c = 0; c < 3; ++c)
+          H[u * 3 + c] = W * (0.5 * (vp[c] * unp + vm[c] * unm) - 0.5 * smax * (vp[c] - vm[c]));
+        pq[u] = q; pt[u] = ti;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+        const int c = o / Nst, rem = o % Nst, ta = rem / N, k = rem % N;
+        double s = 0.0;
+        for (int u = 0; u < cnt; ++u)
+          s = fma(a.fphi[((size_t)code * a.nqf + pq[u]) * N + k] * a.tg[pt[u] * Ng + ta], H[u * 3 + c], s);
+        acc[o] += s;
+      }
+      __syncthreads();
+    }
+  }
+  for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
+    const int c = o / Nst, rem = o % Nst;
+    a.ups[((size_t)c * ne + i) * Nst + rem] = acc[o];
+  }
+}
+
+// max |x[e]| over e >= skip
+__global__ void k_maxabs(int64_t n, int64_t skip, const double* __restrict__ x, double* part) {
+  double m = 0.0;
+  for (int64_t e = skip + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]);
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+
+static FieldArg to_arg(const stdg_field& f) {
+  FieldArg a{};
+  a.kind = f.kind; a.c[0] = f.c[0]; a.c[1] = f.c[1]; a.c[2] = f.c[2]; a.a = f.a; a.d = f.d; a.nu = f.nu;
+  return a;
+}
+
+static MultiIdx make_mi(int p) {
+  MultiIdx mi{};
+  std::vector<int> ex = multi_indices(p);
+  for (size_t k = 0; k < ex.size(); ++k) mi.e[k] = (unsigned char)ex[k];
+  return mi;
+}
+
+static stdg_status ensure_step(stdg_solver* s) {
+  if (s->Vbar) return STDG_OK;
+  const size_t nv = (size_t)s->nf * 3 * s->Nst * sizeof(double);
+  const size_t nb = (size_t)s->ne * 3 * s->Nst * sizeof(double);
+  const size_t np = (size_t)s->ne * s->Nst * sizeof(double);
+  stdg_status e;
+  for (double** p : {&s->Vbar, &s->Vbar_n, &s->Lam, &s->Ups, &s->rhsv})
+    if ((e = dev_alloc(s, (void**)p, nb)) != STDG_OK) return e;
+  for (double** p : {&s->F, &s->Vbc, &s->vtmp})
+    if ((e = dev_alloc(s, (void**)p, nv)) != STDG_OK) return e;
+  if ((e = dev_alloc(s, (void**)&s->Gbc, 3 * nv)) != STDG_OK) return e;
+  for (double** p : {&s->bvec, &s->dp, &s->wk1, &s->wk2})
+    if ((e = dev_alloc(s, (void**)p, np)) != STDG_OK) return e;
+  cudaMemset(s->Vbc, 0, nv);
+  cudaMemset(s->Gbc, 0, 3 * nv);
+  return ensure_krylov(s);
+}
+
+static cudaError_t boundary_data(stdg_solver* s, double t0) {
+  const int CH = 64;
+  size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
+  cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ++s->nlaunch;
+  k_boundary<<<(int)s->nf, 128, smem, s->stream>>>(
+      s->N, s->Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.left, s->dm.right, s->dm.fl, s->dm.bary, s->dm.J,
+      s->dm.detJ, s->dm.fvx, s->dm.normal, s->dm.area, s->C, s->x0h, s->dr.tet_nl_xi, s->dr.tet_nl_w,
+      s->dr.tri_nl_st, s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, make_mi(s->p), to_arg(s->bc), t0, s->dt,
+      s->Vbc, s->Gbc);
+  return cudaGetLastError();
+}
+
+}  // namespace stdg
+
+using namespace stdg;
+
+extern "C" stdg_status stdg_set_initial(stdg_solver* s, const stdg_field* f) {
+  if (!s || !f) { set_error("stdg_set_initial: NULL argument"); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  stdg_status e = ensure_step(s);
+  if (e != STDG_OK) return e;
+  const int CH = 64;
+  size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
+  cudaFuncSetAttribute(k_initial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ++s->nlaunch;
+  k_initial<<<(int)s->nf, 128, smem, s->stream>>>(s->N, s->Ng, s->nq_nl, s->dm.left, s->dm.right, s->dm.fvx,
+                                                  s->dm.bary, s->C, s->x0h, s->dr.tet_nl_xi, s->dr.tet_nl_w,
+                                                  make_mi(s->p), to_arg(*f), s->V);
+  STDG_LAUNCH_CHECK();
+  cudaMemsetAsync(s->P, 0, (size_t)s->ne * s->Nst * sizeof(double), s->stream);
+  s->t = 0.0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("initial projection failed"); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+extern "C" stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* f) {
+  if (!s || !f) { set_error("stdg_set_boundary: NULL argument"); return STDG_EINVAL; }
+  if (f->kind < 0 || f->kind > 2) { set_error("unknown field kind %d", f->kind); return STDG_EINVAL; }
+  s->bc = *f;
+  return STDG_OK;
+}
+
+extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
+                                 stdg_step_stats* stats) {
+  if (!s || n_picard < 1 || n_picard > 8 || !(tol > 0.0) || nu < 0.0) { set_error("stdg_step: invalid argument"); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  auto t_start = std::chrono::steady_clock::now();
+  stdg_status e = ensure_step(s);
+  if (e != STDG_OK) return e;
+  const int N = s->N, Ng = s->Ng, Nst = s->Nst;
+  const int ne = (int)s->ne, nf = (int)s->nf;
+  const int64_t np = (int64_t)ne * Nst;
+  cudaStream_t st = s->stream;
+  GArg g0{}, g1{};
+  MArg K{}, Ki{};
+  for (int a = 0; a < Ng; ++a) { g0.v[a] = s->g0[a]; g1.v[a] = s->g1[a]; }
+  for (int q = 0; q < Ng * Ng; ++q) { K.v[q] = s->K[q]; Ki.v[q] = s->Kinv[q]; }
+  stdg_step_stats local{};
+  // previous slab average and new-slab boundary data
+  ++s->nlaunch;
+  k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar_n);
+  if (boundary_data(s, s->t) != cudaSuccess) { set_error("boundary data launch failed"); return STDG_ECUDA; }
+  // step 0: v^{n+1,0}(x, tau) = v^n(x, 1), p^{n+1,0} = 0
+  ++s->nlaunch;
+  k_trace<<<1216, 256, 0, st>>>(nf, N, Ng, s->dm.right, g1, s->V, s->Vbc, s->vtmp);
+  cudaMemcpyAsync(s->V, s->vtmp, (size_t)nf * 3 * Nst * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(s->P, 0, np * sizeof(double), st);
+  const size_t conv_smem = ((size_t)9 * Nst + 64 * 9) * sizeof(double);
+  cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+  for (int k = 0; k < n_picard; ++k) {
+    // 1. averaging and previous-Picard pressure gradient
+    ++s->nlaunch;
+    k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar);
+    ++s->nlaunch;
+    k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), st>>>(N, Ng, s->dm.left, s->dm.right, s->Q, s->P, s->dt, Ki, s->F);
+    ++s->nlaunch;
+    k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->F, s->Lam);
+    // 2. convection
+    ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
+                s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
+                s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
+                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, to_arg(s->bc), s->t, s->dt, s->Vbar, s->Ups};
+    ++s->nlaunch;
+    k_convection<<<ne, 128, conv_smem, st>>>(ca);
+    // 3. viscous systems (Eq. A1_mod), one per component, initial guess vbar^{n+1,k}
+    ++s->nlaunch;
+    k_visc_rhs<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.t2n, s->dm.detJ, s->Q, g0, g1, K, nu, s->Vbar_n,
+                                   s->Ups, s->Lam, s->Gbc, s->rhsv);
+    if (cudaGetLastError() != cudaSuccess) { set_error("step kernels failed to launch"); return STDG_ECUDA; }
+    int vits = 0;
+    for (int c = 0; c < 3; ++c) {
+      int it = 0;
+      double res = 0.0;
+      e = solve_viscous(s, s->rhsv + (size_t)c * np, s->Vbar + (size_t)c * np, nu, tol, &it, &res);
+      if (e != STDG_OK) return e;
+      vits += it;
+    }
+    // 4. goback
+    ++s->nlaunch;
+    k_goback<<<nf, 128, 0, st>>>(ne, N, Ng, s->dm.left, s->dm.right, s->Mij, s->Vbar, s->Vbc, s->F);
+    // 5. pressure correction (Eq. A2_mod)
+    ++s->nlaunch;
+    if (launch_rhs(ne, N, Ng, s->dm.t2f, s->dm.left, s->Q, s->F, -s->dt, 1, s->bvec, st) != cudaSuccess) {
+      set_error("rhs launch failed"); return STDG_ECUDA;
+    }
+    stdg_solve_stats ss{};
+    e = solve_pressure(s, s->bvec, s->dp, tol, method, &ss);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_axpy<<<1216, 256, 0, st>>>(np, 1.0, s->dp, s->P);
+    // 6. velocity update (Eq. A3_mod)
+    ++s->nlaunch;
+    if (launch_update(nf, N, Ng, s->dm.left, s->dm.right, s->Q, s->F, s->dp, s->dt, s->Kinv.data(), s->V, st) != cudaSuccess) {
+      set_error("update launch failed"); return STDG_ECUDA;
+    }
+    local.press_iters[k] = ss.iterations;
+    local.press_residual[k] = ss.rel_residual;
+    local.visc_iters[k] = vits;
+    local.picard = k + 1;
+  }
+  // diagnostics: discrete divergence Sum_j D_ij v_j on unpinned tets
+  ++s->nlaunch;
+  launch_rhs(ne, N, Ng, s->dm.t2f, s->dm.left, s->Q, s->V, -s->dt, 0, s->bvec, st);
+  ++s->nlaunch;
+  k_maxabs<<<256, 256, 0, st>>>(np, Nst, s->bvec, s->part);
+  std::vector<double> part(256);
+  cudaMemcpyAsync(s->hostbuf + 512, s->part, 256 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("step failed: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+  double mx = 0.0;
+  for (int q = 0; q < 256; ++q) mx = std::fmax(mx, s->hostbuf[512 + q]);
+  local.max_divergence = mx;
+  s->t += s->dt;
+  local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = local;
+  return STDG_OK;
+}

@@ -1,0 +1,179 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Tolerances: one operator application in FP64 agrees to 1e-12 relative (max-norm over the
+output, scaled by the output's max); solves are compared through residuals measured with the
+oracle's operator and against the oracle's direct solution within cond * tol."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from inputs import BeltramiParams, beltrami_velocity, kuhn_mesh
+from oracle import operators as ops
+from oracle.blocks import SpaceTimeDG
+from oracle.mesh import Mesh
+from oracle.step import initial_state, time_step
+
+CASES = [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2), (3, 2, 0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1601_07384_gb300.build import build
+    build()
+
+
+def setup(n, p, pt, dt=0.01, seed=0, **kw):
+    import paper_1601_07384_gb300 as g
+    v, t = kuhn_mesh(n, seed=seed)
+    gs = g.Solver(g.Mesh(v, t), g.Reference(p, pt), dt, **kw)
+    d = SpaceTimeDG(Mesh(v, t), p, pt, dt)
+    return gs, d
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,p,pt", CASES)
+def test_assembled_blocks_match_oracle_operator(n, p, pt):
+    gs, d = setup(n, p, 0, dt=1.0)
+    A = ops.pressure_dense(d, pinned=False) if d.mesh.ne * d.Nst <= 2000 else None
+    if A is None:
+        pytest.skip("dense oracle too large")
+    B = gs.blocks()
+    N = d.N
+    scale = np.abs(A).max()
+    for i in range(d.mesh.ne):
+        assert np.abs(B["Bdiag"][i] - A[i * N:(i + 1) * N, i * N:(i + 1) * N]).max() <= 1e-12 * scale
+    for j in np.nonzero(d.mesh.interior)[0]:
+        l, r = d.mesh.left[j], d.mesh.right[j]
+        assert np.abs(B["Aoff"][j] - A[l * N:(l + 1) * N, r * N:(r + 1) * N]).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("n,p,pt", CASES)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pressure_apply_matches_oracle(n, p, pt, pinned):
+    gs, d = setup(n, p, pt)
+    x = np.random.default_rng(n + 10 * p + pt).standard_normal(d.mesh.ne * d.Nst)
+    y = gs.pressure_apply(torch.from_numpy(x).cuda(), pinned=pinned).cpu().numpy()
+    yo = ops.pressure_apply(d, x, pinned=pinned).ravel()
+    assert rel(y, yo) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,pt", CASES)
+def test_update_rhs_and_moments_match_oracle(n, p, pt):
+    """v = -M^-1 Q dp (Eq. A3_mod with F = 0) compared through the basis-independent moments
+    int phi~ v_h; then b = Sum_j D_ij v_j (Eq. A2_mod right-hand side) = -A dp."""
+    gs, d = setup(n, p, pt)
+    m = d.mesh
+    dp = np.random.default_rng(7).standard_normal((m.ne, d.Nst))
+    zeroF = torch.zeros(m.nf * 3 * d.Nst, dtype=torch.float64, device="cuda")
+    V = gs.velocity_update(zeroF, torch.from_numpy(dp.ravel()).cuda())
+    U = gs.velocity_moments(V).cpu().numpy().reshape(m.nf, 2, 3, d.Nst)
+    Vo = ops.velocity_update(d, np.zeros((m.nf, 3, d.Nst)), dp, np.zeros((m.nf, 3, d.Nst)))
+    Uo = np.zeros_like(U)
+    for j in range(m.nf):
+        fb = d.face_blocks(j)
+        for s in range(len(fb["sides"])):
+            Uo[j, s] = (fb["Mij"][s] @ Vo[j].T).T
+    assert rel(U, Uo) <= 1e-12
+    b = gs.pressure_rhs(V, pinned=False).cpu().numpy()
+    bo = ops.pressure_rhs(d, Vo, pinned=False).ravel()
+    assert rel(b, bo) <= 1e-12
+    Ad = ops.pressure_apply(d, dp, pinned=False).ravel()
+    assert rel(b, -Ad) <= 1e-11
+
+
+@pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1)])
+@pytest.mark.parametrize("method", ["kron_cg", "gmres"])
+def test_solve_matches_direct(n, p, pt, method):
+    from scipy.sparse.linalg import spsolve
+    gs, d = setup(n, p, pt, restart=50, max_iters=50000)
+    b = np.random.default_rng(3).standard_normal((d.mesh.ne, d.Nst))
+    b[0, ops.pin_index(d)] = 0.0
+    tol = 1e-12
+    x, st = gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=tol, method=method)
+    x = x.cpu().numpy()
+    A = ops.pressure_sparse(d)
+    assert np.linalg.norm(b.ravel() - A @ x) <= 2 * tol * np.linalg.norm(b)
+    assert st["rel_residual"] <= 2 * tol
+    xd = spsolve(A.tocsc(), b.ravel())
+    cond = np.linalg.cond(A.toarray()) if A.shape[0] <= 3000 else 1e8
+    assert np.linalg.norm(x - xd) <= 10 * cond * tol * np.linalg.norm(xd)
+
+
+def test_cg_rejects_pt_positive():
+    import paper_1601_07384_gb300 as g
+    gs, d = setup(2, 1, 1)
+    b = torch.zeros(d.mesh.ne * d.Nst, dtype=torch.float64, device="cuda"); b[5] = 1.0
+    with pytest.raises(g.StdgError, match="EINVAL"):
+        gs.solve(b, method="cg")
+
+
+@pytest.mark.parametrize("p,pt,npic", [(1, 0, 2), (2, 1, 2)])
+def test_step_matches_oracle(p, pt, npic):
+    """One full Picard pressure-correction step (Sec. 2.6) on Beltrami data."""
+    import paper_1601_07384_gb300 as g
+    prm = BeltramiParams(nu=0.1)
+    gs, d = setup(2, p, pt, dt=0.01)
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    st = gs.step(prm.nu, npic, method="kron_cg", tol=1e-13)
+    P, V, t = gs.get_state()
+    so = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    # initial projection agrees (through basis-independent moments)
+    so1 = time_step(d, so, prm.nu, npic, lambda x, tt: beltrami_velocity(x, tt, prm), tol=1e-13, method="direct")
+    assert abs(t - 0.01) < 1e-15
+    assert rel(P.cpu().numpy(), so1.P.ravel()) <= 1e-9
+    U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
+    Uo = np.zeros_like(U)
+    for j in range(d.mesh.nf):
+        fb = d.face_blocks(j)
+        for s in range(len(fb["sides"])):
+            Uo[j, s] = (fb["Mij"][s] @ so1.V[j].T).T
+    assert rel(U, Uo) <= 1e-10
+    assert st["max_divergence"] <= 1e-11
+
+
+def test_initial_projection_matches_oracle():
+    import paper_1601_07384_gb300 as g
+    prm = BeltramiParams(nu=0.1)
+    gs, d = setup(2, 3, 1, dt=0.01)
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    _, V, _ = gs.get_state()
+    U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
+    Vo = ops.project_initial(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    Uo = np.zeros_like(U)
+    for j in range(d.mesh.nf):
+        fb = d.face_blocks(j)
+        for s in range(len(fb["sides"])):
+            Uo[j, s] = (fb["Mij"][s] @ Vo[j].T).T
+    assert rel(U, Uo) <= 1e-12
+
+
+def test_large_mesh_sampled_rows():
+    """The workload of the timed benchmark (24^3 hexes x 6 = 82,944 tets, p = 3, p_t = 1):
+    sampled rows of A x computed one by one by the oracle."""
+    import paper_1601_07384_gb300 as g
+    v, t = kuhn_mesh(24, seed=0)
+    gs = g.Solver(g.Mesh(v, t), g.Reference(3, 1), 0.005)
+    om = Mesh(v, t)
+    d = SpaceTimeDG(om, 3, 1, 0.005)
+    x = np.random.default_rng(11).standard_normal((om.ne, d.Nst))
+    y = gs.pressure_apply(torch.from_numpy(x.ravel()).cuda(), pinned=False).cpu().numpy().reshape(om.ne, d.Nst)
+    rows = np.random.default_rng(12).choice(om.ne, 12, replace=False)
+    for i in rows:
+        yi = np.zeros(d.Nst)
+        for f in range(4):
+            j = om.t2f[i, f]
+            if not om.interior[j]:
+                continue
+            fb = d.face_blocks(j)
+            s = fb["sides"].index(i)
+            l, r = fb["sides"]
+            for c in range(3):
+                gg = np.linalg.solve(fb["M"], fb["Q"][0][c] @ x[l] + fb["Q"][1][c] @ x[r])
+                yi += fb["D"][s][c] @ gg
+        assert rel(y[i], yi) <= 1e-12
