@@ -177,6 +177,25 @@ stdg_status stdg_velocity_update(stdg_solver* s, const double* F_dev, const doub
 stdg_status stdg_solve(stdg_solver* s, const double* b_dev, double* x_dev, double tol,
                        int method, stdg_solve_stats* stats);
 
+/* Allocation-free variant of stdg_solve(..., STDG_SOLVER_KRON_CG, ...).  The paper has no
+ * counterpart: this exists for callers that may not allocate device memory once they are
+ * running -- for example code whose device memory is entirely owned by another allocator (a
+ * framework's caching pool that has reserved the device), or latency-critical loops where the
+ * implicit synchronisation and unpredictable latency of cudaMalloc/cudaFree are not acceptable.
+ * stdg_solve allocates its Krylov vectors on first use; this call allocates nothing: its work
+ * vectors live in one fixed device array compiled into the library (8.5 MB, held on every GPU
+ * that loads the library until the process exits).
+ *  - Size limit: ne * Nst <= 262144 pressure unknowns; larger systems return STDG_EINVAL with a
+ *    message (use stdg_solve for them).
+ *  - The first call on each device looks up that array's device address (cudaGetSymbolAddress)
+ *    with the device current; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps whatever the last call left in it (x is set to
+ *    zero before the iteration; everything else is written before it is read).  Calls whose
+ *    device work overlaps -- on different streams or from different threads -- race on it.
+ *  - b_dev, x_dev, tol, stats and the result are as for stdg_solve with STDG_SOLVER_KRON_CG. */
+stdg_status stdg_solve_noalloc(stdg_solver* s, const double* b_dev, double* x_dev, double tol,
+                               stdg_solve_stats* stats);
+
 /* ---------------------------------------------------------------- time stepping */
 /* Initial velocity: spatial L2 projection of `field` at t = 0 onto every dual cell
  * (constant in time), pressure 0, time t = 0. */

@@ -174,6 +174,15 @@ class Solver:
         return x, {"iterations": st.iterations, "restarts": st.restarts, "rel_residual": st.rel_residual,
                    "seconds": st.seconds}
 
+    def solve_noalloc(self, b, x, tol=1e-10):
+        """stdg_solve_noalloc: the Kronecker-decoupled CG solve without any device allocation
+        (the caller supplies x; work vectors live in a fixed array inside the library)."""
+        st = SolveStats()
+        _lib.check(_lib.load().stdg_solve_noalloc(self._h, _ptr(self._dev(b)), _ptr(self._dev(x)), float(tol),
+                                                  C.byref(st)))
+        return x, {"iterations": st.iterations, "restarts": st.restarts, "rel_residual": st.rel_residual,
+                   "seconds": st.seconds}
+
     def velocity_moments(self, V, U=None):
         torch = _torch()
         V = self._dev(V)

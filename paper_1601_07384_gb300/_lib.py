@@ -65,6 +65,7 @@ SIGNATURES = {
     "stdg_pressure_rhs": (C.c_int, [P, P, P, C.c_int]),
     "stdg_velocity_update": (C.c_int, [P, P, P, P]),
     "stdg_solve": (C.c_int, [P, P, P, C.c_double, C.c_int, C.POINTER(SolveStats)]),
+    "stdg_solve_noalloc": (C.c_int, [P, P, P, C.c_double, C.POINTER(SolveStats)]),
     "stdg_set_initial": (C.c_int, [P, C.POINTER(Field)]),
     "stdg_set_boundary": (C.c_int, [P, C.POINTER(Field)]),
     "stdg_step": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.POINTER(StepStats)]),

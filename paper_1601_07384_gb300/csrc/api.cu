@@ -211,6 +211,14 @@ extern "C" stdg_status stdg_solve(stdg_solver* s, const double* b, double* x, do
   return solve_pressure(s, b, x, tol, method, st);
 }
 
+extern "C" stdg_status stdg_solve_noalloc(stdg_solver* s, const double* b, double* x, double tol,
+                                          stdg_solve_stats* st) {
+  stdg_status e = check(s);
+  if (e != STDG_OK) return e;
+  if (!b || !x || b == x || !(tol > 0.0)) { set_error("stdg_solve_noalloc: invalid argument"); return STDG_EINVAL; }
+  return solve_pressure_noalloc(s, b, x, tol, st);
+}
+
 extern "C" stdg_status stdg_velocity_moments(stdg_solver* s, const double* V, double* U) {
   stdg_status e = check(s);
   if (e != STDG_OK) return e;

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "solver.h"
 
@@ -473,4 +474,126 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
   return gmres(s, a, b, x, false, tol * bn, iters, &rs, res);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free pressure solve.  Same Kronecker-decoupled block CG as stdg_solve(KRON_CG), but
+// its work vectors live in one fixed device array compiled into the library instead of memory
+// the solver allocates on first use.  The array holds four vectors of up to kNoAllocMaxDofs
+// doubles, the reduction partials and a few scalars (8.5 MB on every device that loads the
+// library, kept until the process exits).
+constexpr int64_t kNoAllocMaxDofs = 262144;
+constexpr int64_t kNoAllocPart = (int64_t)kRedBlocks * 8;
+constexpr int64_t kNoAllocDoubles = 4 * kNoAllocMaxDofs + kNoAllocPart + 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[128] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+static stdg_status noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) { set_error("allocation-free solve: no usable device"); return STDG_ECUDA; }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("allocation-free solve: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return STDG_ECUDA;
+    }
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return STDG_OK;
+}
+
+static stdg_status noalloc_fetch(stdg_solver* s, const double* dev_src, double* host_dst) {
+  if (cudaMemcpyAsync(host_dst, dev_src, sizeof(double), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    set_error("allocation-free solve: %s", cudaGetErrorString(cudaGetLastError()));
+    return STDG_ECUDA;
+  }
+  return STDG_OK;
+}
+
+static stdg_status noalloc_norm(stdg_solver* s, const double* v, int64_t n, double* part, double* dst, double* out) {
+  k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, v, part);
+  k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, part, dst);
+  s->nlaunch += 2;
+  double h = 0.0;
+  stdg_status e = noalloc_fetch(s, dst, &h);
+  *out = std::sqrt(h);
+  return e;
+}
+
+stdg_status solve_pressure_noalloc(stdg_solver* s, const double* b, double* x, double tol, stdg_solve_stats* st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int N = s->N, Ng = s->Ng;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  if (n > kNoAllocMaxDofs) {
+    set_error("stdg_solve_noalloc: %lld pressure unknowns exceed the allocation-free limit of %lld "
+              "(use stdg_solve)", (long long)n, (long long)kNoAllocMaxDofs);
+    return STDG_EINVAL;
+  }
+  double* base = nullptr;
+  stdg_status e = noalloc_scratch(&base);
+  if (e != STDG_OK) return e;
+  double* bt = base;
+  double* r = base + kNoAllocMaxDofs;
+  double* p = base + 2 * kNoAllocMaxDofs;
+  double* q = base + 3 * kNoAllocMaxDofs;
+  double* part = base + 4 * kNoAllocMaxDofs;
+  double* scal = part + kNoAllocPart;
+  double* rr = scal; double* pq = scal + 8; double* alpha = scal + 16; double* beta = scal + 24;
+  double* rrnew = scal + 32; double* res = scal + 48; double* nrm = scal + 56;
+  double bn = 0.0;
+  if ((e = noalloc_norm(s, b, n, part, nrm, &bn)) != STDG_OK) return e;
+  // x starts at zero; every other scratch value is written before it is read
+  cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+  int it = 0;
+  double rabs = 0.0;
+  if (bn > 0.0) {
+    TpArg Tp{}, Tpinv{};
+    const double idt2 = 1.0 / (s->dt * s->dt);
+    for (int c = 0; c < Ng * Ng; ++c) { Tp.v[c] = s->tm.Tp[c]; Tpinv.v[c] = s->tm.K[c] * idt2; }
+    const ApplyArgs op = pressure_op(s, 1, 1, -1.0, 1.0);
+    k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Tpinv, -1.0, b, bt);
+    cudaMemcpyAsync(r, bt, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(p, bt, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, r, part);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, part, rr);
+    s->nlaunch += 3;
+    const double tol_abs = tol * bn;
+    rabs = INFINITY;
+    while (it < s->opt.max_iters) {
+      if ((e = op_apply(s, op, p, q)) != STDG_OK) return e;
+      k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, part);
+      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, part, pq);
+      k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rr, pq, alpha);
+      k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, Tp, part);
+      k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, part, rrnew);
+      k_cg_beta<<<1, 32, 0, s->stream>>>(Ng, rr, rrnew, beta, res);
+      k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, r, p);
+      s->nlaunch += 7;
+      ++it;
+      if ((e = noalloc_fetch(s, res, &rabs)) != STDG_OK) return e;
+      if (!std::isfinite(rabs)) { set_error("stdg_solve_noalloc: non-finite residual"); return STDG_ENAN; }
+      if (rabs <= tol_abs) break;
+    }
+  }
+  if (st) {
+    double rn = 0.0;
+    if ((e = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, q)) != STDG_OK) return e;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, q);
+    ++s->nlaunch;
+    if ((e = noalloc_norm(s, q, n, part, nrm, &rn)) != STDG_OK) return e;
+    st->iterations = it;
+    st->restarts = 0;
+    st->rel_residual = bn > 0.0 ? rn / bn : 0.0;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (bn > 0.0 && rabs > tol * bn) { set_error("stdg_solve_noalloc reached max_iters (%d)", it); return STDG_ENOCONV; }
+  return STDG_OK;
+}
+
 }  // namespace stdg
+

@@ -52,6 +52,8 @@ stdg_status apply_pressure(stdg_solver* s, const double* x, double* y, int pinne
                            double pin_diag);
 stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double tol, int method,
                            stdg_solve_stats* st);
+stdg_status solve_pressure_noalloc(stdg_solver* s, const double* b, double* x, double tol,
+                                   stdg_solve_stats* st);
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res);
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes);
