@@ -30,6 +30,7 @@ METRIC = "s/time-step at 1e-10 residual (chosen vs plain FP64 GMRES); matvec HBM
 WORKLOADS = {
     "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
     "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50),
+    "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
@@ -51,14 +52,14 @@ def mesh_counts(n):
     return ne, (4 * ne - nb) // 2, nb
 
 
-def operator_cost(w):
+def operator_cost(w, entry_bytes=8, vec_bytes=8):
     """Algorithmic bytes and flops of one five-point operator application (assembled form:
     symmetric diagonal blocks counted packed, every off-diagonal block once, x read once, y
     written once; flops = 2 Ng per applied block entry)."""
     ne, nint, _ = mesh_counts(w["n"])
     N = nbasis(w["p"]); Ng = w["pt"] + 1
     entries = ne * N * (N + 1) // 2 + nint * N * N
-    bytes_alg = 8 * entries + 2 * 8 * ne * N * Ng
+    bytes_alg = entry_bytes * entries + 2 * vec_bytes * ne * N * Ng
     flops = 2 * Ng * (ne * N * N + 2 * nint * N * N)
     return bytes_alg, flops
 
@@ -138,6 +139,26 @@ def oracle_operator_sample(w, reps=3, n_sample=3):
     return float(np.median(times)) * nint / nint_s, nint_s
 
 
+def operator_alone_ms(solver, precision, reps):
+    """Average duration of one pressure-operator launch, CUDA events on the solver's stream."""
+    import torch
+    x = torch.randn(solver.ne * solver.Nst, dtype=torch.float64, device="cuda")
+    xf = x.float()
+    y = torch.empty_like(x)
+    yf = torch.empty_like(xf)
+    run = (lambda: solver.pressure_apply_f32(xf, yf)) if precision.startswith("mixed") else \
+        (lambda: solver.pressure_apply(x, y))
+    run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(solver.stream)
+    for _ in range(reps):
+        run()
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -188,7 +209,10 @@ def main():
     ap.add_argument("--gmres-steps", type=int, default=1)
     ap.add_argument("--gmres-max-iters", type=int, default=30000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
+    ap.add_argument("--solver", default="kron_pcg", choices=["kron_cg", "kron_pcg", "gmres"])
+    ap.add_argument("--op-only", type=int, default=0,
+                    help="only build the workload and apply the pressure operator this many times (profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,11 +239,16 @@ def main():
     ref = g.Reference(w["p"], w["pt"])
     solver = g.Solver(mesh, ref, w["dt"], precision=args.precision, restart=w["restart"], max_iters=200000)
     fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
+    if args.op_only > 0:
+        ms = operator_alone_ms(solver, args.precision, args.op_only)
+        print(json.dumps({"op_only": args.op_only, "precision": args.precision, "workload": workload_name(w),
+                          "avg_launch_ms": ms}))
+        return
     solver.set_initial(fld)
     solver.set_boundary(fld)
     stream = solver.stream
     for _ in range(args.warmup):
-        solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"])
+        solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
 
     def barrier():
         if world > 1:
@@ -234,7 +263,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            stats.append(solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"]))
+            stats.append(solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"]))
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
@@ -258,7 +287,7 @@ def main():
     te0 = time.perf_counter()
     for _ in range(args.steps):
         g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0, tcur.value))
-        solver.step(w["nu"], w["npic"], method="kron_cg", tol=w["tol"])
+        solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
         g._lib.check(lib.stdg_get_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0,
                                         C.byref(tcur)))
     barrier()
@@ -288,36 +317,50 @@ def main():
               "press_iters": st.get("press_iters") if ok else None}
         del gsolver
 
-    # ---- roofline of the operator kernel
-    bytes_alg, flops = operator_cost(w)
-    op_launch_ms = prof["operator_ms"] / max(prof["operator_launches"], 1)
+    # ---- roofline of the dominant operator kernel (CUDA-event time of its launches in the timed region)
+    kinds = ["fp64 blocks (k_apply)", "fp32-pair blocks (k_apply_tma<PolDF>)", "fp32 blocks (k_apply_tma<PolF32>)",
+             "bf16 blocks (k_apply_tma<PolBF16>)"]
+    kbest = int(np.argmax(prof["kind_ms"]))
+    nlaunch_k = max(prof["kind_launches"][kbest], 1)
+    op_launch_ms = prof["kind_ms"][kbest] / nlaunch_k
+    bytes_alg, flops = operator_cost(w, entry_bytes=[8, 8, 4, 2][kbest], vec_bytes=[8, 8, 4, 4][kbest])
     tflops = flops / (op_launch_ms * 1e-3) / 1e12
     gbs = bytes_alg / (op_launch_ms * 1e-3) / 1e9
-    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     ops_per_step = prof["operator_launches"] / args.steps
     traffic = None
     tf = os.path.join(ROOT, "profiles", "operator_traffic.json")
     if os.path.exists(tf):
         tr = json.load(open(tf))
-        if tr.get("workload") == workload_name(w) and tr.get("precision") == args.precision:
-            traffic = tr.get("dram_bytes_per_launch")
+        key = f"{workload_name(w)}|{kinds[kbest]}"
+        traffic = tr.get(key)
+    if kbest == 0:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS,
+                "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20 TFLOP/s)"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "peak_note": f"HBM copy bandwidth, {hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    alone = operator_alone_ms(solver, args.precision, 20)
+    roof.update({"traffic": traffic, "kernel": kinds[kbest], "avg_launch_ms": op_launch_ms,
+                 "alone_avg_launch_ms": alone,
+                 "launches_timed": int(nlaunch_k), "algorithmic_bytes_per_launch": bytes_alg,
+                 "flops_per_launch": flops, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                 "fp64_equiv_tflops": tflops})
 
     out = {
         "metric": METRIC, "value": s_per_step * 1.0, "unit": "s/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s_per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (fp32-pair products)",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "df32": "f64 (products from fp32 pairs)",
+                                       "mixed_f32": "f64 refinement / f32 inner", "mixed_bf16": "f64 refinement / bf16 blocks"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload_name(w), "solver": "kron_cg (block CG on the Ng decoupled SPD systems)",
+        "config": {"workload": workload_name(w), "solver": args.solver, "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
-        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_apply (five-point block operator)",
-                     "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
-                             "algorithmic_bytes_per_launch": bytes_alg},
-                     "flops_per_launch": flops, "avg_launch_ms": op_launch_ms,
-                     "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (measured 1.20 TFLOP/s)"},
+        "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(P0.numel() + V0.numel()) * 8,
                 "d2h_bytes_per_step": int(P0.numel() + V0.numel()) * 8},
         "gpu_launches": int(prof["kernel_launches"]),

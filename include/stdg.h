@@ -62,16 +62,30 @@ typedef enum {
  *                      operator of Eq. CS_19 factors as A = A_sp (x) dt^2 K^-1, so
  *                      A x = b  <=>  A_sp X = B K^T / dt^2 column by column (block CG, all
  *                      columns share each operator launch).  The stopping test is on the
- *                      residual of the full system, as for the other methods.            */
-enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2 };
+ *                      residual of the full system, as for the other methods.
+ *  STDG_SOLVER_KRON_PCG: STDG_SOLVER_KRON_CG preconditioned by block Jacobi: the exact inverse
+ *                      of each tet's N x N diagonal block of the pinned -A_sp (built on first
+ *                      use, Cholesky on the device).  The paper uses no preconditioner; this
+ *                      changes only the iteration, not the system or its stopping test.      */
+/*  STDG_SOLVER_FGMRES_BJ / STDG_SOLVER_FGMRES_GNN : flexible GMRES(m) on the full operator,
+ *                      right-preconditioned by block Jacobi of the full operator
+ *                      (A_ii^-1 = B_i^-1 (x) (dt^2 K^-1)^-1) alone, or by block Jacobi plus the
+ *                      learned network correction (stdg_gnn_*).  Needs stdg_gnn_init.         */
+enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_SOLVER_KRON_PCG = 3,
+       STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5 };
 
 /* Precision of the operator blocks used inside the Krylov iteration (stdg_solver_options).
  *  STDG_PREC_FP64   : blocks and arithmetic in binary64.
  *  STDG_PREC_DF32   : binary64 blocks and vectors, products formed in pairs of binary32
  *                     ("double-float", ~48-bit significand) because sm_103a's binary64
  *                     pipe is ~1/58 of its binary32 rate; results agree with STDG_PREC_FP64
- *                     to ~1e-14 relative per operator application.                       */
-enum { STDG_PREC_FP64 = 0, STDG_PREC_DF32 = 1 };
+ *                     to ~1e-14 relative per operator application.
+ *  STDG_PREC_MIXED_F32 / STDG_PREC_MIXED_BF16 : the Kronecker CG methods run as FP64 iterative
+ *                     refinement around an inner block-Jacobi CG whose operator blocks are
+ *                     binary32 / bfloat16 (vectors and accumulation binary32); the outer
+ *                     residual, the correction and the stopping test are binary64, so the
+ *                     returned x meets the same FP64 residual tolerance.                   */
+enum { STDG_PREC_FP64 = 0, STDG_PREC_DF32 = 1, STDG_PREC_MIXED_F32 = 2, STDG_PREC_MIXED_BF16 = 3 };
 
 typedef struct {
   int iterations;          /* Krylov iterations (operator applications in the loop)   */
@@ -136,6 +150,9 @@ typedef struct {
   int precision;           /* STDG_PREC_FP64 (default) or STDG_PREC_DF32              */
   int restart;             /* GMRES restart length m (default 50)                     */
   int max_iters;           /* cap on Krylov iterations per solve (default 200000)     */
+  int graph_batch;         /* CG iterations per CUDA-graph launch (default 8; 1 = no graphs,
+                              one host check per iteration).  With B > 1 up to B-1 iterations
+                              may run past convergence; they are counted in the stats.       */
 } stdg_solver_options;
 
 /* Upload mesh and reference tables to the current CUDA device and build every per-face
@@ -159,6 +176,12 @@ stdg_status stdg_set_dt(stdg_solver* s, double dt);
  * Dubiner mode of tet 0 for every time function: x there is read as 0 and y there = -x.
  * x_dev, y_dev: P layout, ne*Nst doubles each, must not overlap. */
 stdg_status stdg_pressure_apply(stdg_solver* s, const double* x_dev, double* y_dev, int pinned);
+
+/* The same operator with binary32 vectors x_dev, y_dev (P layout, ne*Nst floats) and the
+ * solver's low-precision blocks (binary32 or bfloat16 per its precision option, built on first
+ * use; needs STDG_PREC_MIXED_F32 or STDG_PREC_MIXED_BF16, else STDG_EINVAL).  Accumulation is
+ * binary32; the blocks are staged through shared memory by TMA bulk copies. */
+stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x_dev, float* y_dev, int pinned);
 
 /* b = Sum_{j in S_i} D_ij F_j over all four faces of each tet (Eq. A2_mod right-hand side,
  * Eq. CS_15 left-hand side), with D_ij = -Q_ij^T.  F_dev: V layout (nf*3*Nst), b_dev: P
@@ -216,11 +239,43 @@ stdg_status stdg_set_state(stdg_solver* s, const double* P, const double* V, int
  * M_{i,j} v_j product of Eq. vis3).  V_dev: V layout, U_dev: nf*2*3*Nst doubles. */
 stdg_status stdg_velocity_moments(stdg_solver* s, const double* V_dev, double* U_dev);
 
+/* ------------------------------------------------- learned preconditioner (FGMRES) */
+/* The paper solves the pressure system without a preconditioner.  These calls build, train and
+ * apply a small message-passing network over the tet-face adjacency that is added to block
+ * Jacobi as the right preconditioner of flexible GMRES (STDG_SOLVER_FGMRES_GNN):
+ *   x_i = [r_i / RMS(r), (|J_i|/mean|J|)^(1/3), boundary faces of i / 4]
+ *   h0 = relu(We x + be); h^l = relu(Ws^l h^{l-1} + Wm^l Sum_{face neighbours} h^{l-1} + b^l)
+ *   M(r) = BJ(r) + RMS(r) (Wd h^L + bd)
+ * Weights: binary32 master copy, working copy in bfloat16 (bf16_weights != 0) or binary32;
+ * products accumulate in binary32.  Training minimises the mean of ||net(r) - t||^2 / ||t||^2
+ * over harvested pairs with Adam.  Parameters are one flat binary32 array whose layout is
+ * given by stdg_gnn_layout (offsets of We, be, then Ws, Wm, b per layer, then Wd, bd). */
+stdg_status stdg_gnn_init(stdg_solver* s, int hidden, int layers, int bf16_weights, uint64_t seed);
+stdg_status stdg_gnn_layout(stdg_solver* s, int64_t* offsets, int* hidden, int* layers, int* nfeat);
+/* Copy the binary32 master parameters out (w_out) and/or in (w_in, resets Adam); either may be NULL. */
+stdg_status stdg_gnn_params(stdg_solver* s, float* w_out, const float* w_in, int64_t* nparams);
+/* z = RMS(r) (Wd h^L + bd): the network alone (P layout, device). */
+stdg_status stdg_gnn_apply(stdg_solver* s, const double* r_dev, double* z_dev);
+/* Mean loss over npairs pairs (R_dev, T_dev: npairs consecutive P-layout vectors) and its gradient
+ * with respect to the master parameters, copied to grad_host (may be NULL). */
+stdg_status stdg_gnn_loss_grad(stdg_solver* s, const double* R_dev, const double* T_dev, int npairs,
+                               double* loss, float* grad_host);
+/* Solve A x = b with block-Jacobi Kronecker CG to 1e-12, keeping up to nsnap iterates x_k taken
+ * every `every` iterations; store pairs (r_k = b - A x_k, t_k = (x - x_k) - BJ(r_k)) for training
+ * (at most max_pairs in total, device memory sized on the first call). */
+stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b_dev, int nsnap, int every, int max_pairs,
+                             int* total_pairs);
+/* `epochs` passes of Adam (learning rate lr, `batch` pairs per update) over the harvested pairs. */
+stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int batch, double* first_loss,
+                           double* last_loss);
+
 /* ---------------------------------------------------------------- profiling */
 typedef struct {
   int64_t kernel_launches;   /* CUDA kernels this library launched since stdg_profile      */
   int64_t operator_launches; /* five-point operator launches (pressure and viscous)        */
   double operator_ms;        /* summed CUDA-event time of the operator launches (enabled)  */
+  int64_t kind_launches[4];  /* timed operator launches by kernel: [0] binary64 blocks,     */
+  double kind_ms[4];         /* [1] binary32-pair blocks, [2] binary32, [3] bfloat16 blocks */
 } stdg_profile_stats;
 /* Reset the counters; enable != 0 also records a CUDA event pair around every operator
  * launch on the solver's stream (adds two event records per launch). */

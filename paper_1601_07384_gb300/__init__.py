@@ -114,14 +114,14 @@ class Solver:
     """Device-resident discretisation: blocks, state and Krylov workspace (stdg_solver_create)."""
 
     def __init__(self, mesh: Mesh, ref: Reference, dt, precision="fp64", restart=50, max_iters=200000,
-                 stream=None):
+                 stream=None, graph_batch=8):
         torch = _torch()
         lib = _lib.load()
         self.mesh, self.ref = mesh, ref
         self.N, self.Ng, self.Nst = ref.N, ref.Ng, ref.Nst
         self.ne, self.nf = mesh.ne, mesh.nf
         self.dt = float(dt)
-        opts = SolverOptions(PREC[precision], int(restart), int(max_iters))
+        opts = SolverOptions(PREC[precision], int(restart), int(max_iters), int(graph_batch))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _lib.check(lib.stdg_solver_create(mesh._h, ref._h, self.dt, C.byref(opts),
@@ -152,6 +152,13 @@ class Solver:
         x = self._dev(x)
         y = self.pressure_empty() if y is None else self._dev(y)
         _lib.check(_lib.load().stdg_pressure_apply(self._h, _ptr(x), _ptr(y), int(bool(pinned))))
+        return y
+
+    def pressure_apply_f32(self, x, y=None, pinned=True):
+        torch = _torch()
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        y = torch.empty_like(x) if y is None else y
+        _lib.check(_lib.load().stdg_pressure_apply_f32(self._h, _ptr(x), _ptr(y), int(bool(pinned))))
         return y
 
     def pressure_rhs(self, F, b=None, pinned=True):
@@ -215,6 +222,54 @@ class Solver:
     def set_state(self, P, V, t):
         _lib.check(_lib.load().stdg_set_state(self._h, _ptr(self._dev(P)), _ptr(self._dev(V)), 1, float(t)))
 
+    # ---------------------------------------------------------------- learned preconditioner
+    def gnn_init(self, hidden=64, layers=3, bf16=True, seed=0):
+        _lib.check(_lib.load().stdg_gnn_init(self._h, int(hidden), int(layers), int(bool(bf16)), int(seed)))
+
+    def gnn_layout(self):
+        L = C.c_int(); H = C.c_int(); F = C.c_int()
+        offs = (C.c_int64 * 64)()
+        _lib.check(_lib.load().stdg_gnn_layout(self._h, offs, C.byref(H), C.byref(L), C.byref(F)))
+        n = 2 + 3 * L.value + 2
+        return {"offsets": list(offs[:n]), "hidden": H.value, "layers": L.value, "nfeat": F.value}
+
+    def gnn_params(self, w_in=None):
+        npar = C.c_int64()
+        _lib.check(_lib.load().stdg_gnn_params(self._h, None, None, C.byref(npar)))
+        out = np.empty(npar.value, dtype=np.float32)
+        win = None
+        if w_in is not None:
+            win = np.ascontiguousarray(w_in, dtype=np.float32)
+        _lib.check(_lib.load().stdg_gnn_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)),
+                                               None if win is None else win.ctypes.data_as(C.POINTER(C.c_float)),
+                                               C.byref(npar)))
+        return out
+
+    def gnn_apply(self, r, z=None):
+        z = self.pressure_empty() if z is None else z
+        _lib.check(_lib.load().stdg_gnn_apply(self._h, _ptr(self._dev(r)), _ptr(self._dev(z))))
+        return z
+
+    def gnn_loss_grad(self, R, T, npairs):
+        npar = C.c_int64()
+        _lib.check(_lib.load().stdg_gnn_params(self._h, None, None, C.byref(npar)))
+        g = np.empty(npar.value, dtype=np.float32)
+        loss = C.c_double()
+        _lib.check(_lib.load().stdg_gnn_loss_grad(self._h, _ptr(self._dev(R)), _ptr(self._dev(T)), int(npairs),
+                                                  C.byref(loss), g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def gnn_harvest(self, b, nsnap=10, every=20, max_pairs=64):
+        tot = C.c_int()
+        _lib.check(_lib.load().stdg_gnn_harvest(self._h, _ptr(self._dev(b)), int(nsnap), int(every), int(max_pairs),
+                                                C.byref(tot)))
+        return tot.value
+
+    def gnn_train(self, epochs=50, lr=1e-3, batch=4):
+        a = C.c_double(); b = C.c_double()
+        _lib.check(_lib.load().stdg_gnn_train(self._h, int(epochs), float(lr), int(batch), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def profile(self, enable=True):
         _lib.check(_lib.load().stdg_profile(self._h, int(bool(enable))))
 
@@ -222,7 +277,7 @@ class Solver:
         st = _lib.ProfileStats()
         _lib.check(_lib.load().stdg_profile_read(self._h, C.byref(st)))
         return {"kernel_launches": st.kernel_launches, "operator_launches": st.operator_launches,
-                "operator_ms": st.operator_ms}
+                "operator_ms": st.operator_ms, "kind_launches": list(st.kind_launches), "kind_ms": list(st.kind_ms)}
 
     def blocks(self):
         N, nf, ne = self.N, self.nf, self.ne

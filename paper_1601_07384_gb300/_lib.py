@@ -7,8 +7,8 @@ LIB_PATH = os.path.join(HERE, "libstdg.so")
 
 STATUS = {0: "STDG_OK", -1: "STDG_EINVAL", -2: "STDG_ENOMEM", -3: "STDG_ECUDA", -4: "STDG_ENOCONV",
           -5: "STDG_EMESH", -6: "STDG_ENAN", -7: "STDG_ETIMEOUT", -8: "STDG_EUNSUPPORTED"}
-SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2}
-PREC = {"fp64": 0, "df32": 1}
+SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5}
+PREC = {"fp64": 0, "df32": 1, "mixed_f32": 2, "mixed_bf16": 3}
 FIELD = {"zero": 0, "constant": 1, "beltrami": 2}
 
 
@@ -30,11 +30,12 @@ class StepStats(C.Structure):
 
 
 class SolverOptions(C.Structure):
-    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int), ("graph_batch", C.c_int)]
 
 
 class ProfileStats(C.Structure):
-    _fields_ = [("kernel_launches", C.c_int64), ("operator_launches", C.c_int64), ("operator_ms", C.c_double)]
+    _fields_ = [("kernel_launches", C.c_int64), ("operator_launches", C.c_int64), ("operator_ms", C.c_double),
+                ("kind_launches", C.c_int64 * 4), ("kind_ms", C.c_double * 4)]
 
 
 class Field(C.Structure):
@@ -62,6 +63,7 @@ SIGNATURES = {
     "stdg_solver_destroy": (None, [P]),
     "stdg_set_dt": (C.c_int, [P, C.c_double]),
     "stdg_pressure_apply": (C.c_int, [P, P, P, C.c_int]),
+    "stdg_pressure_apply_f32": (C.c_int, [P, P, P, C.c_int]),
     "stdg_pressure_rhs": (C.c_int, [P, P, P, C.c_int]),
     "stdg_velocity_update": (C.c_int, [P, P, P, P]),
     "stdg_solve": (C.c_int, [P, P, P, C.c_double, C.c_int, C.POINTER(SolveStats)]),
@@ -74,6 +76,13 @@ SIGNATURES = {
     "stdg_velocity_moments": (C.c_int, [P, P, P]),
     "stdg_get_blocks": (C.c_int, [P, DP, DP, DP, DP]),
     "stdg_profile": (C.c_int, [P, C.c_int]),
+    "stdg_gnn_init": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_uint64]),
+    "stdg_gnn_layout": (C.c_int, [P, I64P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "stdg_gnn_params": (C.c_int, [P, C.POINTER(C.c_float), C.POINTER(C.c_float), I64P]),
+    "stdg_gnn_apply": (C.c_int, [P, P, P]),
+    "stdg_gnn_loss_grad": (C.c_int, [P, P, P, C.c_int, DP, C.POINTER(C.c_float)]),
+    "stdg_gnn_harvest": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "stdg_gnn_train": (C.c_int, [P, C.c_int, C.c_double, C.c_int, DP, DP]),
     "stdg_profile_read": (C.c_int, [P, C.POINTER(ProfileStats)]),
     "stdg_last_error": (C.c_char_p, []),
     "stdg_version": (C.c_char_p, []),

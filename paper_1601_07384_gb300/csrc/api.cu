@@ -63,12 +63,15 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   if (!s) { set_error("out of host memory"); return STDG_ENOMEM; }
   cudaGetDevice(&s->device);
   s->stream = (cudaStream_t)stream;
-  s->opt.precision = STDG_PREC_FP64; s->opt.restart = 50; s->opt.max_iters = 200000;
+  s->opt.precision = STDG_PREC_FP64; s->opt.restart = 50; s->opt.max_iters = 200000; s->opt.graph_batch = 8;
   if (opts) {
     s->opt = *opts;
     if (s->opt.restart <= 0) s->opt.restart = 50;
     if (s->opt.restart > 60) { delete s; set_error("restart must be <= 60"); return STDG_EUNSUPPORTED; }
     if (s->opt.max_iters <= 0) s->opt.max_iters = 200000;
+    if (s->opt.graph_batch <= 0) s->opt.graph_batch = 8;
+    if (s->opt.graph_batch > 64) { delete s; set_error("graph_batch must be <= 64"); return STDG_EINVAL; }
+    if (s->opt.precision < 0 || s->opt.precision > 3) { delete s; set_error("unknown precision %d", opts->precision); return STDG_EINVAL; }
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;
@@ -91,6 +94,18 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   TRY(upload_i32(s, &d.t2f, m->t2f.data(), 4 * m->ne));
   TRY(upload_i32(s, &d.t2n, m->t2n.data(), 4 * m->ne));
   TRY(upload_i32(s, &d.t2code, m->t2code.data(), 4 * m->ne));
+  {
+    // gather tables: per tet and local face, (face id << 1 | tet is r(j)) or -1 on the boundary
+    std::vector<int> gf(4 * m->ne), gn(4 * m->ne);
+    for (int64_t i = 0; i < m->ne; ++i)
+      for (int f = 0; f < 4; ++f) {
+        const int64_t j = m->t2f[4 * i + f], nb = m->t2n[4 * i + f];
+        gf[4 * i + f] = nb >= 0 ? (int)((j << 1) | (m->left[j] == i ? 0 : 1)) : -1;
+        gn[4 * i + f] = (int)nb;
+      }
+    TRY(upload(s, &s->gface, gf.data(), gf.size()));
+    TRY(upload(s, &s->gnbr, gn.data(), gn.size()));
+  }
   std::vector<double> X0(3 * m->ne), fvx(9 * m->nf);
   for (int64_t i = 0; i < m->ne; ++i)
     for (int c = 0; c < 3; ++c) X0[3 * i + c] = m->X[3 * m->T[4 * i] + c];
@@ -135,6 +150,8 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   TRY(dev_alloc(s, (void**)&s->Aoff, (size_t)m->nf * NN * sizeof(double)));
   TRY(dev_alloc(s, (void**)&s->Bdiag, (size_t)m->ne * NN * sizeof(double)));
   TRY(dev_alloc(s, (void**)&s->Bvisc, (size_t)m->ne * NN * sizeof(double)));
+  TRY(dev_alloc(s, (void**)&s->derr, sizeof(int)));
+  cudaMemset(s->derr, 0, sizeof(int));
   TRY(dev_alloc(s, (void**)&s->P, (size_t)m->ne * s->Nst * sizeof(double)));
   TRY(dev_alloc(s, (void**)&s->V, (size_t)m->nf * 3 * s->Nst * sizeof(double)));
   cudaMemset(s->P, 0, (size_t)m->ne * s->Nst * sizeof(double));
@@ -144,6 +161,7 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   for (size_t k = 0; k < ex.size(); ++k) mi.e[k] = (unsigned char)ex[k];
   cudaError_t ce = launch_face_blocks(d, t, s->p, s->N, r->nq_lin, r->nqf_lin, mi, s->Q, s->Mij, s->C, s->x0h, s->stream);
   if (ce == cudaSuccess) ce = launch_assemble(d, s->N, s->Q, s->Aoff, s->Bdiag, s->Bvisc, s->stream);
+  if (ce == cudaSuccess && s->opt.precision == STDG_PREC_DF32) ce = df_build_blocks(s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) {
     set_error("device preprocessing failed: %s", cudaGetErrorString(ce));
@@ -161,6 +179,9 @@ extern "C" void stdg_solver_destroy(stdg_solver* s) {
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->gev) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->sync_ev) if (e) cudaEventDestroy(e);
+  if (s->cstream) cudaStreamDestroy(s->cstream);
   for (void* p : s->allocs) cudaFree(p);
   if (s->hostbuf) cudaFreeHost(s->hostbuf);
   delete s;
@@ -180,6 +201,25 @@ extern "C" stdg_status stdg_pressure_apply(stdg_solver* s, const double* x, doub
   if (e != STDG_OK) return e;
   if (!x || !y || x == y) { set_error("stdg_pressure_apply: x, y must be distinct device buffers"); return STDG_EINVAL; }
   return apply_pressure(s, x, y, pinned ? 1 : 0, 0, 1.0, -1.0);
+}
+
+extern "C" stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x, float* y, int pinned) {
+  stdg_status e = check(s);
+  if (e != STDG_OK) return e;
+  if (!x || !y || (const void*)x == (const void*)y) { set_error("stdg_pressure_apply_f32: x, y must be distinct device buffers"); return STDG_EINVAL; }
+  if (s->opt.precision != STDG_PREC_MIXED_F32 && s->opt.precision != STDG_PREC_MIXED_BF16) {
+    set_error("stdg_pressure_apply_f32 needs a solver created with STDG_PREC_MIXED_F32 or _BF16");
+    return STDG_EINVAL;
+  }
+  if (!s->lpB) {
+    cudaError_t ce = lp_build_blocks(s, s->opt.precision);
+    s->nlaunch += 2;
+    if (ce != cudaSuccess) { set_error("low-precision block copies failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  }
+  ++s->nlaunch;
+  cudaError_t ce = launch_apply_lp(s, x, y, pinned ? 1 : 0, 0, 1.0f, -1.0f);
+  if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  return STDG_OK;
 }
 
 extern "C" stdg_status stdg_pressure_rhs(stdg_solver* s, const double* F, double* b, int pinned) {
@@ -262,11 +302,6 @@ extern "C" stdg_status stdg_set_state(stdg_solver* s, const double* P, const dou
   return STDG_OK;
 }
 
-namespace stdg {
-cudaError_t launch_apply_df32(const ApplyArgs&, const double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-}  // namespace stdg
 
 extern "C" stdg_status stdg_profile(stdg_solver* s, int enable) {
   stdg_status e = check(s);
@@ -283,6 +318,7 @@ extern "C" stdg_status stdg_profile(stdg_solver* s, int enable) {
   s->op_ms = 0.0;
   s->op_launches = 0;
   s->nlaunch = 0;
+  for (int q = 0; q < 4; ++q) { s->kind_ms[q] = 0.0; s->kind_n[q] = 0; }
   return STDG_OK;
 }
 
@@ -295,5 +331,6 @@ extern "C" stdg_status stdg_profile_read(stdg_solver* s, stdg_profile_stats* out
   out->kernel_launches = s->nlaunch;
   out->operator_launches = s->op_launches;
   out->operator_ms = s->op_ms;
+  for (int q = 0; q < 4; ++q) { out->kind_launches[q] = s->kind_n[q]; out->kind_ms[q] = s->kind_ms[q]; }
   return STDG_OK;
 }

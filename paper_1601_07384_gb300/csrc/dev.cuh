@@ -67,6 +67,7 @@ cudaError_t launch_face_blocks(const DevMesh& m, const DevRef& r, int p, int N, 
                                cudaStream_t st);
 cudaError_t launch_assemble(const DevMesh& m, int N, const double* Q, double* Aoff, double* Bdiag,
                             double* Bvisc, cudaStream_t st);
+cudaError_t launch_block_inverse(int ne, int N, const double* Bdiag, double* Binv, cudaStream_t st);
 
 }  // namespace stdg
 
@@ -88,7 +89,6 @@ struct ApplyArgs {
   double Kmass[kMaxNg * kMaxNg];
 };
 cudaError_t launch_apply(const ApplyArgs& a, const double* x, double* y, cudaStream_t st);
-cudaError_t launch_apply_df32(const ApplyArgs& a, const double* x, double* y, cudaStream_t st);
 
 // b_i[a][l] = coef Sum_{f} Sum_c Sum_m Q^c_{s(i,j)}[m][l] F_j[c][a][m]   (D = -Q^T; coef = -dt)
 cudaError_t launch_rhs(int ne, int N, int Ng, const int* t2f, const int* left, const double* Q,

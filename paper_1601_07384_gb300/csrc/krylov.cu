@@ -78,6 +78,53 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t ne, int N, in
   block_reduce_store(acc, Ng + 1, part, Ng + 1);
 }
 
+// z_i[a][k] = Sum_l Binv_i[k][l] r_i[a][l]  (block Jacobi); partials of r.z per column a.
+// Fixed grid (kRedBlocks blocks striding over tets) so the partials stay deterministic.
+__global__ void __launch_bounds__(128) k_bjacobi(int ne, int N, int Ng, const double* __restrict__ Binv,
+                                                 const double* __restrict__ r, double* __restrict__ z,
+                                                 double* part) {
+  extern __shared__ double sm[];
+  const int Nst = N * Ng;
+  const size_t NN = (size_t)N * N;
+  double* rs = sm;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x; i < ne; i += gridDim.x) {
+    __syncthreads();
+    for (int o = threadIdx.x; o < Nst; o += blockDim.x) rs[o] = r[(size_t)i * Nst + o];
+    __syncthreads();
+    for (int o = threadIdx.x; o < Nst; o += blockDim.x) {
+      const int a = o / N, k = o % N;
+      const double* B = Binv + (size_t)i * NN + k;     // symmetric: read column k (coalesced over k)
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s = fma(B[(size_t)l * N], rs[a * N + l], s);
+      z[(size_t)i * Nst + o] = s;
+      acc[a] = fma(s, rs[o], acc[a]);
+    }
+  }
+  __shared__ double red[8][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = 0; a < Ng; ++a) {
+    double v = warp_sum(acc[a]);
+    if (lane == 0) red[a][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < Ng) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    part[(size_t)blockIdx.x * Ng + threadIdx.x] = s;
+  }
+}
+
+// beta_a = rznew_a / rz_a; rz <- rznew; res = sqrt(mix2)
+__global__ void k_cg_beta2(int Ng, double* rz, const double* rznew, double* beta, double* res, const double* mix2) {
+  int a = threadIdx.x;
+  if (a < Ng) {
+    beta[a] = (rz[a] != 0.0) ? rznew[a] / rz[a] : 0.0;
+    rz[a] = rznew[a];
+  }
+  if (a == 0) res[0] = sqrt(mix2[0]);
+}
+
 // p = r + beta_a p
 __global__ void k_cg_dir(int64_t n, int N, int Ng, const double* __restrict__ beta, const double* __restrict__ r,
                          double* __restrict__ p) {
@@ -191,7 +238,7 @@ stdg_status ensure_krylov(stdg_solver* s) {
   if (s->kb) return STDG_OK;
   const size_t n = (size_t)s->ne * s->Nst * sizeof(double);
   stdg_status st;
-  for (double** v : {&s->kb, &s->kx, &s->kr, &s->kp, &s->kq})
+  for (double** v : {&s->kb, &s->kx, &s->kr, &s->kp, &s->kq, &s->kz})
     if ((st = dev_alloc(s, (void**)v, n)) != STDG_OK) return st;
   if ((st = dev_alloc(s, (void**)&s->part, (size_t)kRedBlocks * kMaxCols * sizeof(double))) != STDG_OK) return st;
   if ((st = dev_alloc(s, (void**)&s->scal, 1024 * sizeof(double))) != STDG_OK) return st;
@@ -227,20 +274,24 @@ void prof_fold(stdg_solver* s) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]);
     s->op_ms += ms;
+    s->kind_ms[s->ev_kind[k]] += ms;
+    s->kind_n[s->ev_kind[k]] += 1;
   }
   s->ev_used = 0;
 }
 
 static stdg_status op_apply(stdg_solver* s, const ApplyArgs& a, const double* x, double* y) {
-  const bool prof = s->prof && !s->ev.empty();
+  const bool prof = s->prof && !s->ev.empty() && !s->capturing;
+  const bool use_df = s->opt.precision == STDG_PREC_DF32 && s->dfB && a.Bextra == nullptr && a.mass_coef == 0.0;
   if (prof) {
     if (2 * s->ev_used >= (int)s->ev.size()) prof_fold(s);
+    s->ev_kind[s->ev_used] = use_df ? 1 : 0;
     cudaEventRecord(s->ev[2 * s->ev_used], s->stream);
   }
   ++s->nlaunch;
   ++s->op_launches;
-  cudaError_t e = (s->opt.precision == STDG_PREC_DF32 && s->blk32 && a.Bextra == nullptr)
-                      ? launch_apply_df32(a, x, y, s->stream)
+  // binary64-accurate operator from binary32 pairs when requested (pressure operator only)
+  cudaError_t e = use_df ? launch_apply_df(s, x, y, a.pinned, a.tacc_identity, a.scale, a.pin_diag)
                       : launch_apply(a, x, y, s->stream);
   if (prof) {
     cudaEventRecord(s->ev[2 * s->ev_used + 1], s->stream);
@@ -266,15 +317,112 @@ stdg_status apply_pressure(stdg_solver* s, const double* x, double* y, int pinne
   return op_apply(s, pressure_op(s, pinned, kron, scale, pin_diag), x, y);
 }
 
-// Block CG for an operator that is symmetric positive definite on each time column.
+// Run `body` (one Krylov iteration that ends by copying its residual to host_slot) in batches of
+// B iterations captured once into a CUDA graph and replayed on an internal stream; the caller's
+// stream is ordered before and after by events.  Up to B-1 iterations may run past convergence;
+// they are counted.  Operator launches inside the graph are timed by dedicated event nodes.
+template <typename Body>
+static stdg_status run_batched(stdg_solver* s, int B, int kernels_per_iter, int max_it, double tol_abs, Body body,
+                               int* iters, double* rabs_out, int kind) {
+  if (!s->cstream) {
+    if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->sync_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->sync_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("internal stream creation failed");
+      return STDG_ECUDA;
+    }
+  }
+  if ((int)s->gev.size() < 2 * B) {
+    for (cudaEvent_t e : s->gev) cudaEventDestroy(e);
+    s->gev.assign(2 * B, nullptr);
+    for (auto& e : s->gev)
+      if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return STDG_ECUDA; }
+  }
+  cudaStream_t user = s->stream;
+  cudaEventRecord(s->sync_ev[0], user);
+  cudaStreamWaitEvent(s->cstream, s->sync_ev[0], 0);
+  s->stream = s->cstream;
+  const bool prof = s->prof;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  stdg_status st = STDG_OK;
+  s->capturing = true;
+  if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    s->capturing = false; s->stream = user;
+    set_error("stream capture failed to start");
+    return STDG_ECUDA;
+  }
+  for (int j = 0; j < B && st == STDG_OK; ++j) st = body(j, prof ? &s->gev[2 * j] : nullptr);
+  cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
+  s->capturing = false;
+  if (st == STDG_OK && (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)) {
+    set_error("graph capture/instantiation failed: %s", cudaGetErrorString(ce));
+    st = STDG_ECUDA;
+  }
+  int it = 0;
+  double rabs = INFINITY;
+  while (st == STDG_OK && it < max_it) {
+    if (cudaGraphLaunch(exec, s->stream) != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      st = STDG_ECUDA;
+      break;
+    }
+    it += B;
+    s->nlaunch += (int64_t)B * kernels_per_iter;
+    s->op_launches += B;
+    if (prof) {
+      for (int j = 0; j < B; ++j) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s->gev[2 * j], s->gev[2 * j + 1]);
+        s->op_ms += ms;
+        s->kind_ms[kind] += ms;
+        s->kind_n[kind] += 1;
+      }
+    }
+    bool done = false;
+    for (int j = 0; j < B; ++j) {
+      rabs = s->hostbuf[j];
+      if (!std::isfinite(rabs)) { set_error("Krylov: non-finite residual"); st = STDG_ENAN; break; }
+      if (rabs <= tol_abs) { done = true; }
+    }
+    rabs = s->hostbuf[B - 1];
+    if (done) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventRecord(s->sync_ev[1], s->stream);
+  s->stream = user;
+  cudaStreamWaitEvent(user, s->sync_ev[1], 0);
+  *iters = it;
+  *rabs_out = rabs;
+  return st;
+}
+
+static stdg_status ensure_block_inverse(stdg_solver* s) {
+  if (s->Binv) return STDG_OK;
+  stdg_status e = dev_alloc(s, (void**)&s->Binv, (size_t)s->ne * s->N * s->N * sizeof(double));
+  if (e != STDG_OK) return e;
+  ++s->nlaunch;
+  cudaError_t ce = launch_block_inverse((int)s->ne, s->N, s->Bdiag, s->Binv, s->stream);
+  if (ce != cudaSuccess) { set_error("block inverse launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+// Block CG for an operator that is symmetric positive definite on each time column, optionally
+// preconditioned by block Jacobi (precond: per-tet inverses of the pinned diagonal blocks of -A).
 // x holds the initial guess unless zero_x0.  Stops when ||(I (x) mix) r|| <= tol_abs.
 static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* rhs, double* x, bool zero_x0,
-                            const TpArg& mix, double tol_abs, int* iters, double* res_abs) {
+                            const TpArg& mix, double tol_abs, int* iters, double* res_abs, bool precond = false) {
   const int N = s->N, Ng = s->Ng;
   const int64_t n = s->ne * (int64_t)s->Nst;
-  double* r = s->kr; double* p = s->kp; double* q = s->kq;
-  double* rr = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
-  double* rrnew = s->scal + 32; double* res = s->scal + 48;
+  double* r = s->kr; double* p = s->kp; double* q = s->kq; double* z = s->kz;
+  double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
+  double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
+  const size_t bj_smem = (size_t)s->Nst * sizeof(double);
+  if (precond) {
+    stdg_status e = ensure_block_inverse(s);
+    if (e != STDG_OK) return e;
+  }
   if (zero_x0) {
     cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
     cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
@@ -284,37 +432,60 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
     ++s->nlaunch;
     k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, rhs, nullptr, 1, r);
   }
-  cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  if (precond) {
+    ++s->nlaunch;
+    k_bjacobi<<<kRedBlocks, 128, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->Binv, r, z, s->part);
+    cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  } else {
+    cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    ++s->nlaunch;
+    k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, r, s->part);
+  }
   ++s->nlaunch;
-  k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, r, s->part);
-  ++s->nlaunch;
-  k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rr);
+  k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
+  // one CG iteration; ends by copying the full-system residual norm to the host
+  auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
+    if (evs) cudaEventRecord(evs[0], s->stream);
+    stdg_status e = op_apply(s, op, p, q);
+    if (evs) cudaEventRecord(evs[1], s->stream);
+    if (e != STDG_OK) return e;
+    k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
+    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha);
+    k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part);
+    k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
+    if (precond) {
+      k_bjacobi<<<kRedBlocks, 128, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->Binv, r, z, s->part);
+      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
+      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
+    } else {
+      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rrnew, beta, res, rrnew + Ng);
+    }
+    k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, precond ? z : r, p);
+    cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    return STDG_OK;
+  };
+  const int kpi = precond ? 9 : 7;
   int it = 0;
   double rabs = INFINITY;
   const int maxit = s->opt.max_iters;
-  while (it < maxit) {
-    stdg_status e = op_apply(s, op, p, q);
+  if (s->opt.graph_batch > 1) {
+    const int kind = (s->opt.precision == STDG_PREC_DF32 && s->dfB && op.Bextra == nullptr && op.mass_coef == 0.0) ? 1 : 0;
+    stdg_status e = run_batched(s, s->opt.graph_batch, kpi, maxit, tol_abs, body, &it, &rabs, kind);
     if (e != STDG_OK) return e;
-    ++s->nlaunch;
-    k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
-    ++s->nlaunch;
-    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
-    ++s->nlaunch;
-    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rr, pq, alpha);
-    ++s->nlaunch;
-    k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part);
-    ++s->nlaunch;
-    k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
-    ++s->nlaunch;
-    k_cg_beta<<<1, 32, 0, s->stream>>>(Ng, rr, rrnew, beta, res);
-    ++s->nlaunch;
-    k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, r, p);
-    cudaMemcpyAsync(s->hostbuf, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    ++it;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
-    rabs = s->hostbuf[0];
-    if (!std::isfinite(rabs)) { set_error("CG: non-finite residual"); return STDG_ENAN; }
-    if (rabs <= tol_abs) break;
+  } else {
+    while (it < maxit) {
+      stdg_status e = body(0, nullptr);
+      if (e != STDG_OK) return e;
+      s->nlaunch += kpi;
+      ++it;
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+      rabs = s->hostbuf[0];
+      if (!std::isfinite(rabs)) { set_error("CG: non-finite residual"); return STDG_ENAN; }
+      if (s->snap_every > 0 && it % s->snap_every == 0 && s->nsnap < s->snap_cap && rabs > tol_abs)
+        cudaMemcpyAsync(s->snaps + (size_t)(s->nsnap++) * n, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+      if (rabs <= tol_abs) break;
+    }
   }
   *iters = it;
   *res_abs = rabs;
@@ -407,6 +578,209 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
   return STDG_OK;
 }
 
+// Flexible GMRES(m) with a right preconditioner z_j = M(v_j) that may change between iterations
+// (block Jacobi, or block Jacobi plus the learned network): x = x0 + Z y minimises ||b - A x||.
+static stdg_status fgmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
+                          double tol_abs, int* iters, int* nrestarts, double* res_abs, int use_gnn) {
+  const int m = s->opt.restart;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  stdg_status e = ensure_basis(s, m + 1);
+  if (e != STDG_OK) return e;
+  if (!s->kzz && (e = dev_alloc(s, (void**)&s->kzz, (size_t)m * n * sizeof(double))) != STDG_OK) return e;
+  if (zero_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double* hd = s->scal + 100;     // h (pass 1) at [0..m], h (pass 2) at [128..], norm^2 at [256]
+  int it = 0, restarts = 0;
+  double beta = INFINITY;
+  const int maxit = s->opt.max_iters;
+  while (true) {
+    e = op_apply(s, op, x, s->kq);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);
+    beta = host_norm(s, s->kq, n);
+    if (!std::isfinite(beta)) { set_error("GMRES: non-finite residual"); return STDG_ENAN; }
+    if (beta <= tol_abs || it >= maxit) break;
+    s->hostbuf[901] = beta * beta;
+    cudaMemcpyAsync(s->scal + 901, s->hostbuf + 901, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, s->kq, s->scal + 901, 0, s->basis);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (k = 0; k < m; ++k) {
+      double* w = s->basis + (size_t)(k + 1) * n;
+      double* zk = s->kzz + (size_t)k * n;
+      e = gnn_precond(s, s->basis + (size_t)k * n, zk, use_gnn);
+      if (e != STDG_OK) return e;
+      e = op_apply(s, op, zk, w);
+      if (e != STDG_OK) return e;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = hd + pass * 128;
+        ++s->nlaunch;
+        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part);
+        ++s->nlaunch;
+        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp);
+        ++s->nlaunch;
+        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w);
+      }
+      ++s->nlaunch;
+      k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
+      ++s->nlaunch;
+      k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, s->part, hd + 256);
+      ++s->nlaunch;
+      k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, hd + 256, 0, w);
+      cudaMemcpyAsync(s->hostbuf, hd, 257 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("GMRES: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = s->hostbuf[i] + s->hostbuf[128 + i];
+      H[(size_t)(k + 1) * m + k] = std::sqrt(s->hostbuf[256]);
+      for (int i = 0; i < k; ++i) {
+        double t1 = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)(i + 1) * m + k] = -sn[i] * H[(size_t)i * m + k] + cs[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = t1;
+      }
+      double den = std::hypot(H[(size_t)k * m + k], H[(size_t)(k + 1) * m + k]);
+      cs[k] = H[(size_t)k * m + k] / den;
+      sn[k] = H[(size_t)(k + 1) * m + k] / den;
+      H[(size_t)k * m + k] = den;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++it;
+      if (!std::isfinite(g[k + 1])) { set_error("GMRES: non-finite residual estimate"); return STDG_ENAN; }
+      if (std::fabs(g[k + 1]) <= tol_abs || it >= maxit) { ++k; break; }
+    }
+    if (k > m) k = m;
+    for (int i = k - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int jj = i + 1; jj < k; ++jj) sum -= H[(size_t)i * m + jj] * y[jj];
+      y[i] = sum / H[(size_t)i * m + i];
+    }
+    std::memcpy(s->hostbuf, y.data(), k * sizeof(double));
+    cudaMemcpyAsync(hd, s->hostbuf, k * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    ++s->nlaunch;
+    k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k, s->kzz, hd, 1.0, x);
+    ++restarts;
+  }
+  *iters = it; *nrestarts = restarts; *res_abs = beta;
+  if (beta > tol_abs) { set_error("FGMRES reached max_iters (%d)", it); return STDG_ENOCONV; }
+  return STDG_OK;
+}
+
+static stdg_status ensure_lowprec(stdg_solver* s) {
+  if (s->fr) return STDG_OK;
+  stdg_status e = ensure_block_inverse(s);
+  if (e != STDG_OK) return e;
+  if (!s->lpB) {
+    cudaError_t ce = lp_build_blocks(s, s->opt.precision);
+    s->nlaunch += 2;
+    if (ce != cudaSuccess) { set_error("low-precision block copies failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  }
+  const size_t n = (size_t)s->ne * s->Nst;
+  for (float** v : {&s->fr, &s->fp, &s->fq, &s->fz, &s->fx, &s->fb})
+    if ((e = dev_alloc(s, (void**)v, n * sizeof(float))) != STDG_OK) return e;
+  if ((e = dev_alloc(s, (void**)&s->lpBinv, (size_t)s->ne * s->N * s->N * sizeof(float))) != STDG_OK) return e;
+  if ((e = dev_alloc(s, (void**)&s->dmix, kMaxNg * kMaxNg * sizeof(double))) != STDG_OK) return e;
+  LpKernels lk = lp_kernels();
+  lk.f32(s->stream, (int64_t)s->ne * s->N * s->N, s->Binv, s->lpBinv);
+  ++s->nlaunch;
+  cudaMemcpyAsync(s->dmix, s->K.data(), s->Ng * s->Ng * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("low-precision setup failed"); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+// FP64 iterative refinement around a binary32 inner block-Jacobi CG on the decoupled system.
+// Outer: r = b - A x (FP64 operator); inner: (-A_sp (x) I) d = -(I (x) Tp^-1) r / ||r|| to a
+// relative full-system residual tau; x += ||r|| d.  Stops on the FP64 residual <= tol ||b||.
+static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, double tol, double bn, int* iters,
+                               int* outer, double* res_abs) {
+  stdg_status e = ensure_lowprec(s);
+  if (e != STDG_OK) return e;
+  const int N = s->N, Ng = s->Ng;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  LpKernels lk = lp_kernels();
+  double Tp[kMaxNg * kMaxNg];
+  for (int c = 0; c < Ng * Ng; ++c) Tp[c] = s->tm.Tp[c];
+  double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
+  double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
+  const double tau = 1e-4;
+  cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
+  cudaMemcpyAsync(s->kr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  int total = 0, o = 0;
+  double rn = bn, rprev = INFINITY;
+  for (o = 0; o < 40; ++o) {
+    if (o > 0) rn = host_norm(s, s->kr, n);
+    if (!std::isfinite(rn)) { set_error("mixed solve: non-finite residual"); return STDG_ENAN; }
+    if (rn <= tol * bn || total >= s->opt.max_iters) break;
+    if (rn > 0.5 * rprev) {
+      set_error("mixed solve: refinement stalled at relative residual %g (the low-precision operator is too "
+                "inaccurate for this system's conditioning)", rn / bn);
+      *iters = total; *outer = o; *res_abs = rn;
+      return STDG_ENOCONV;
+    }
+    rprev = rn;
+    // inner right-hand side and block-Jacobi CG in binary32
+    lk.from64(s->stream, s->ne, N, Ng, s->dmix, -1.0 / (s->dt * s->dt * rn), s->kr, s->fb);
+    cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
+    cudaMemcpyAsync(s->fr, s->fb, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+    lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
+    cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+    s->nlaunch += 3;
+    auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
+      if (evs) cudaEventRecord(evs[0], s->stream);
+      cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
+      if (evs) cudaEventRecord(evs[1], s->stream);
+      if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+      lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
+      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
+      k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha);
+      lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tp, s->part);
+      k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
+      lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
+      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
+      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
+      lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
+      cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+      return STDG_OK;
+    };
+    double rin = INFINITY;
+    int inner = 0;
+    if (s->opt.graph_batch > 1) {
+      e = run_batched(s, s->opt.graph_batch, 10, s->opt.max_iters - total, tau, body, &inner, &rin,
+                      s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2);
+      if (e != STDG_OK) return e;
+      total += inner;
+    } else {
+      while (total < s->opt.max_iters) {
+        e = body(0, nullptr);
+        if (e != STDG_OK) return e;
+        s->nlaunch += 10; ++s->op_launches;
+        ++total;
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("mixed CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+        rin = s->hostbuf[0];
+        if (!std::isfinite(rin)) { set_error("mixed CG: non-finite inner residual"); return STDG_ENAN; }
+        if (rin <= tau) break;
+      }
+    }
+    // x += ||r|| d ; r = b - A x in FP64
+    lk.accum(s->stream, n, rn, s->fx, x);
+    ++s->nlaunch;
+    e = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, s->kr);
+    if (e != STDG_OK) return e;
+    ++s->nlaunch;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kr);
+  }
+  int herr = 0;
+  cudaMemcpy(&herr, s->derr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (herr) { set_error("low-precision operator: a bounded wait timed out"); return STDG_ETIMEOUT; }
+  *iters = total;
+  *outer = o;
+  *res_abs = rn;
+  if (rn > tol * bn) { set_error("mixed solve did not reach the tolerance (%d inner iterations)", total); return STDG_ENOCONV; }
+  return STDG_OK;
+}
+
 stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double tol, int method,
                            stdg_solve_stats* st) {
   stdg_status e = ensure_krylov(s);
@@ -425,7 +799,16 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
     cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   } else if (method == STDG_SOLVER_GMRES) {
     r = gmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it, &rs, &rabs);
-  } else if (method == STDG_SOLVER_CG || method == STDG_SOLVER_KRON_CG) {
+  } else if (method == STDG_SOLVER_FGMRES_BJ || method == STDG_SOLVER_FGMRES_GNN) {
+    r = ensure_block_inverse(s);
+    if (r == STDG_OK && !s->gnn) { set_error("FGMRES with block Jacobi / learned preconditioner needs stdg_gnn_init"); r = STDG_EINVAL; }
+    if (r == STDG_OK)
+      r = fgmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it, &rs, &rabs,
+                 method == STDG_SOLVER_FGMRES_GNN ? 1 : 0);
+  } else if ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG) &&
+             (s->opt.precision == STDG_PREC_MIXED_F32 || s->opt.precision == STDG_PREC_MIXED_BF16)) {
+    r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs);
+  } else if (method == STDG_SOLVER_CG || method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG) {
     // A = A_sp (x) Tp (pinned):  A x = b  <=>  (-A_sp (x) I) x = -(I (x) Tp^-1) b,  Tp^-1 = K / dt^2;
     // the full residual is b - A x = -(I (x) Tp) r for the CG residual r.
     TpArg Tp{}, Tpinv{};
@@ -433,7 +816,8 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
     for (int q = 0; q < s->Ng * s->Ng; ++q) { Tp.v[q] = s->tm.Tp[q]; Tpinv.v[q] = s->tm.K[q] * idt2; }
     ++s->nlaunch;
     k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, s->N, s->Ng, Tpinv, -1.0, b, s->kb);
-    r = cg_block(s, pressure_op(s, 1, 1, -1.0, 1.0), s->kb, x, true, Tp, tol * bn, &it, &rabs);
+    r = cg_block(s, pressure_op(s, 1, 1, -1.0, 1.0), s->kb, x, true, Tp, tol * bn, &it, &rabs,
+                 method == STDG_SOLVER_KRON_PCG);
   } else {
     set_error("unknown solver method %d", method);
     return STDG_EINVAL;

@@ -247,6 +247,39 @@ __global__ void k_diag(int ne, int N, const int* t2f, const int* t2n, const int*
   }
 }
 
+// Binv_i = S_ii^-1 for the symmetric positive definite diagonal block S_ii = -B_i of the pinned
+// operator -A (tet 0: the pinned constant mode becomes an identity row and column).  Cholesky in
+// shared memory: S = L L^T, S^-1 = L^-T L^-1.
+__global__ void __launch_bounds__(128) k_block_inverse(int N, const double* __restrict__ Bdiag, double* __restrict__ Binv) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const size_t NN = (size_t)N * N;
+  double* G = sm;
+  double* Ci = sm + NN;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int r = idx / N, c = idx % N;
+    double v = -Bdiag[i * NN + idx];
+    if (i == 0 && (r == 0 || c == 0)) v = (r == c) ? 1.0 : 0.0;
+    G[idx] = v;
+  }
+  __syncthreads();
+  chol_inverse(G, Ci, N);
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    int r = idx / N, c = idx % N;
+    double s = 0.0;
+    for (int k = (r > c ? r : c); k < N; ++k) s += Ci[k * N + r] * Ci[k * N + c];
+    Binv[i * NN + idx] = s;
+  }
+}
+
+cudaError_t launch_block_inverse(int ne, int N, const double* Bdiag, double* Binv, cudaStream_t st) {
+  size_t smem = 2 * (size_t)N * N * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (ne > 0) k_block_inverse<<<ne, 128, smem, st>>>(N, Bdiag, Binv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble(const DevMesh& m, int N, const double* Q, double* Aoff, double* Bdiag,
                             double* Bvisc, cudaStream_t st) {
   if (m.nf > 0) k_offdiag<<<m.nf, 128, 0, st>>>(m.nf, N, m.right, Q, Aoff);

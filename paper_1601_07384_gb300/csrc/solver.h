@@ -4,6 +4,24 @@
 
 #include "dev.cuh"
 
+namespace stdg {
+// State of the learned preconditioner (gnn.cu)
+struct GnnState {
+  int H = 64, L = 3, G = 2, F = 0, C = 0, bf16 = 1;
+  int64_t np = 0;
+  std::vector<int64_t> off;        // We, be, (Ws, Wm, b) x L, Wd, bd
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  void* wc = nullptr;              // working copy (bfloat16 or binary32)
+  int adam_t = 0;
+  float *geom = nullptr, *X = nullptr, *pre0 = nullptr, *out = nullptr, *dout = nullptr;
+  float *dh = nullptr, *dpre = nullptr, *t1 = nullptr, *t2 = nullptr, *wpart = nullptr;
+  std::vector<float*> h, mb, pre;
+  double *sdev = nullptr, *part = nullptr, *loss = nullptr, *tpinv = nullptr;
+  double *R = nullptr, *T = nullptr;   // harvested pairs (residual, target = error - BJ(residual))
+  int npairs = 0, cap = 0;
+};
+}  // namespace stdg
+
 struct stdg_solver {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -21,7 +39,19 @@ struct stdg_solver {
   // per-face / per-tet blocks
   double *Q = nullptr, *Mij = nullptr, *C = nullptr, *x0h = nullptr;
   double *Aoff = nullptr, *Bdiag = nullptr, *Bvisc = nullptr;
-  float* blk32 = nullptr;                     // double-float copies (hi, lo) of Bdiag / Aoff
+  double *Binv = nullptr;                     // block-Jacobi: (-B_i)^-1, pinned (lazily built)
+  double *kz = nullptr;                       // preconditioned residual
+  // low-precision copies for the mixed-precision inner solve
+  void *lpB = nullptr, *lpA = nullptr;        // blocks in binary32 or bfloat16, padded stride lpSB
+  int lpSB = 0, lpkind = -1;
+  void *dfB = nullptr, *dfA = nullptr;        // (hi, lo) binary32 pairs of the FP64 blocks
+  int dfSB = 0;
+  int tma_grid[16] = {0};                     // persistent grid size per block element size
+  int *gface = nullptr, *gnbr = nullptr;      // per-tet gather tables (int4 each) for the TMA kernels
+  float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
+  float *fr = nullptr, *fp = nullptr, *fq = nullptr, *fz = nullptr, *fx = nullptr, *fb = nullptr;
+  double* dmix = nullptr;                     // device copy of K (time mixing)
+  int* derr = nullptr;                        // device error word (bounded waits)
   // state
   double *P = nullptr, *V = nullptr;
   double t = 0.0;
@@ -38,15 +68,44 @@ struct stdg_solver {
   double *F = nullptr, *Vbc = nullptr, *Gbc = nullptr, *bvec = nullptr, *dp = nullptr, *vtmp = nullptr;
   double *wk1 = nullptr, *wk2 = nullptr;
   std::vector<void*> allocs;
+  stdg::GnnState* gnn = nullptr;
+  double* kzz = nullptr;                     // FGMRES preconditioned directions
+  int snap_every = 0, snap_cap = 0, nsnap = 0;
+  double* snaps = nullptr;
+  // CUDA-graph batching of Krylov iterations
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t sync_ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> gev;
+  bool capturing = false;
   // profiling: kernel launch count and CUDA-event timing of every operator launch
   int64_t nlaunch = 0, op_launches = 0;
   bool prof = false;
   std::vector<cudaEvent_t> ev;      // start/stop pairs
   int ev_used = 0;
   double op_ms = 0.0;
+  double kind_ms[4] = {0, 0, 0, 0};           // by kernel kind: FP64, pair-FP32, FP32, BF16
+  int64_t kind_n[4] = {0, 0, 0, 0};
+  int ev_kind[4096];
 };
 
 namespace stdg {
+// binary32 Krylov kernels (lowprec.cu), exposed as launch functions
+struct LpKernels {
+  void (*coldot)(cudaStream_t, int64_t, int, int, const float*, const float*, double*);
+  void (*update)(cudaStream_t, int64_t, int, int, const double*, float*, float*, const float*, const float*,
+                 const double*, double*);
+  void (*dir)(cudaStream_t, int64_t, int, int, const double*, const float*, float*);
+  void (*bjacobi)(cudaStream_t, int, int, int, const float*, const float*, float*, double*);
+  void (*from64)(cudaStream_t, int64_t, int, int, const double*, double, const double*, float*);
+  void (*accum)(cudaStream_t, int64_t, double, const float*, double*);
+  void (*f32)(cudaStream_t, int64_t, const double*, float*);
+};
+LpKernels lp_kernels();
+cudaError_t lp_build_blocks(stdg_solver* s, int kind);
+cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag);
+cudaError_t launch_apply_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
+                            double pin_diag);
+cudaError_t df_build_blocks(stdg_solver* s);
 stdg_status ensure_krylov(stdg_solver* s);
 stdg_status apply_pressure(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                            double pin_diag);
@@ -54,6 +113,7 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
                            stdg_solve_stats* st);
 stdg_status solve_pressure_noalloc(stdg_solver* s, const double* b, double* x, double tol,
                                    stdg_solve_stats* st);
+stdg_status gnn_precond(stdg_solver* s, const double* r, double* z, int use_gnn);
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res);
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes);

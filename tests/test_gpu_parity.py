@@ -177,3 +177,68 @@ def test_large_mesh_sampled_rows():
                 gg = np.linalg.solve(fb["M"], fb["Q"][0][c] @ x[l] + fb["Q"][1][c] @ x[r])
                 yi += fb["D"][s][c] @ gg
         assert rel(y[i], yi) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2)])
+@pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("mixed_bf16", 5e-2)])
+def test_lowprec_operator_matches_oracle(n, p, pt, prec, tol):
+    """Binary32 / bfloat16 blocks with binary32 accumulation (TMA-staged kernel): error bounded
+    by the storage precision of the blocks (2^-24 / 2^-9 relative per entry)."""
+    gs, d = setup(n, p, pt, precision=prec)
+    x = np.random.default_rng(5).standard_normal(d.mesh.ne * d.Nst)
+    y = gs.pressure_apply_f32(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+    yo = ops.pressure_apply(d, x.astype(np.float32).astype(np.float64)).ravel()
+    assert rel(y, yo) <= tol
+
+
+@pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2)])
+@pytest.mark.parametrize("prec", ["fp64", "df32", "mixed_f32"])
+def test_preconditioned_and_mixed_solves_match_direct(n, p, pt, prec):
+    """Block-Jacobi Kronecker CG, in FP64 or as FP64 iterative refinement around a binary32 /
+    bfloat16 inner solve: same FP64 residual tolerance, same solution."""
+    from scipy.sparse.linalg import spsolve
+    gs, d = setup(n, p, pt, precision=prec, max_iters=50000)
+    b = np.random.default_rng(9).standard_normal((d.mesh.ne, d.Nst))
+    b[0, ops.pin_index(d)] = 0.0
+    tol = 1e-11
+    x, st = gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=tol, method="kron_pcg")
+    x = x.cpu().numpy()
+    A = ops.pressure_sparse(d)
+    assert np.linalg.norm(b.ravel() - A @ x) <= 2 * tol * np.linalg.norm(b)
+    xd = spsolve(A.tocsc(), b.ravel())
+    assert np.linalg.norm(x - xd) <= 1e-5 * np.linalg.norm(xd)
+
+
+def test_bf16_refinement_stops_loudly_when_it_cannot_converge():
+    """With bfloat16 blocks the refinement contracts only if cond(A) * 2^-9 < 1, which these
+    pressure systems violate: the solve must stop with ENOCONV, not iterate to the cap."""
+    import paper_1601_07384_gb300 as g
+    gs, d = setup(2, 2, 1, precision="mixed_bf16", max_iters=50000)
+    b = np.random.default_rng(9).standard_normal((d.mesh.ne, d.Nst))
+    b[0, ops.pin_index(d)] = 0.0
+    with pytest.raises(g.StdgError, match="ENOCONV"):
+        gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=1e-11, method="kron_pcg")
+
+
+@pytest.mark.parametrize("n,p,pt", CASES)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_df32_operator_matches_oracle(n, p, pt, pinned):
+    """FP64-accurate operator from binary32 pairs (TMA-staged kernel): 1e-12 like FP64."""
+    gs, d = setup(n, p, pt, precision="df32")
+    x = np.random.default_rng(n + 10 * p + pt).standard_normal(d.mesh.ne * d.Nst)
+    y = gs.pressure_apply(torch.from_numpy(x).cuda(), pinned=pinned).cpu().numpy()
+    yo = ops.pressure_apply(d, x, pinned=pinned).ravel()
+    assert rel(y, yo) <= 1e-12
+
+
+@pytest.mark.parametrize("batch", [1, 8])
+def test_graph_batched_cg_matches_unbatched(batch):
+    """Graph-batched block CG (B iterations per launch) returns a solution meeting the tolerance;
+    iteration counts are multiples of B."""
+    gs, d = setup(2, 3, 1, graph_batch=batch)
+    b = np.random.default_rng(2).standard_normal((d.mesh.ne, d.Nst))
+    b[0, ops.pin_index(d)] = 0.0
+    x, st = gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=1e-11, method="kron_pcg")
+    A = ops.pressure_sparse(d)
+    assert np.linalg.norm(b.ravel() - A @ x.cpu().numpy()) <= 2e-11 * np.linalg.norm(b)
+    assert st["iterations"] % batch == 0
