@@ -31,6 +31,7 @@ WORKLOADS = {
     "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
     "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50),
     "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
+    "learned": dict(n=12, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
@@ -199,6 +200,51 @@ def reference_arm(args, w, world, rank):
                       "wall_s": wall}))
 
 
+def learned_protocol(args, g, torch):
+    """Harvest residual/error pairs from the pressure solves of the first steps, train the network
+    on the GPU, then run the next steps with FGMRES + (block Jacobi + network), FGMRES + block
+    Jacobi, and plain GMRES(50), from the same state."""
+    from inputs import kuhn_mesh
+    w = WORKLOADS["learned"]
+    v, t = kuhn_mesh(w["n"], seed=0)
+    mesh = g.Mesh(v, t)
+    ref = g.Reference(w["p"], w["pt"])
+    s = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=20000, graph_batch=1)
+    fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
+    s.set_initial(fld); s.set_boundary(fld)
+    s.gnn_init(hidden=64, layers=3, bf16=True, seed=0)
+    s.gnn_autoharvest(nsnap=6, every=40, max_pairs=64)
+    n_train, n_eval = 3, 2
+    for _ in range(n_train):
+        s.step(w["nu"], w["npic"], method="kron_pcg", tol=w["tol"])
+    s.gnn_autoharvest(0, 0, 0)
+    t0 = time.perf_counter()
+    l0, l1 = s.gnn_train(epochs=150, lr=2e-3, batch=4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    P0, V0, tt = s.get_state()
+    res = {}
+    for method in ["fgmres_gnn", "fgmres_bj", "gmres"]:
+        s.set_state(P0, V0, tt)
+        its, secs, fb, ok = [], [], 0, True
+        for _ in range(n_eval):
+            torch.cuda.synchronize(); a = time.perf_counter()
+            try:
+                st = s.step(w["nu"], w["npic"], method=method, tol=w["tol"])
+                its.append(st["press_iters"]); fb += st["fallbacks"]
+            except g.StdgError as exc:
+                ok = False; its.append(str(exc)[:80])
+            torch.cuda.synchronize(); secs.append(time.perf_counter() - a)
+            if not ok:
+                break
+        res[method] = {"s_per_step": float(np.median(secs)), "press_iters": its, "converged": ok, "fallbacks": fb}
+    print(json.dumps({"learned_preconditioner": {
+        "workload": workload_name(w), "train_steps": n_train, "eval_steps": n_eval,
+        "train_loss_first_last": [l0, l1], "train_seconds": t_train,
+        "network": "3 message-passing layers, hidden 64, bf16 weights, fp32 accumulation, added to block Jacobi",
+        "results": res}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +257,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
     ap.add_argument("--solver", default="kron_pcg", choices=["kron_cg", "kron_pcg", "gmres"])
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-preconditioner protocol: harvest + train on early steps, evaluate FGMRES later")
     ap.add_argument("--op-only", type=int, default=0,
                     help="only build the workload and apply the pressure operator this many times (profiling)")
     args = ap.parse_args()
@@ -234,6 +282,8 @@ def main():
     import paper_1601_07384_gb300 as g
     from inputs import kuhn_mesh
 
+    if args.learned:
+        return learned_protocol(args, g, torch)
     v, t = kuhn_mesh(w["n"], seed=0)
     mesh = g.Mesh(v, t)
     ref = g.Reference(w["p"], w["pt"])

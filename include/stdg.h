@@ -92,6 +92,8 @@ typedef struct {
   int restarts;            /* GMRES restarts                                          */
   double rel_residual;     /* ||b - A x|| / ||b|| of the returned x                   */
   double seconds;          /* wall time of the call                                   */
+  int fallback;            /* 1 if FGMRES with the learned preconditioner failed (stall /
+                              non-finite value) and plain GMRES produced the result          */
 } stdg_solve_stats;
 
 typedef struct {
@@ -101,6 +103,7 @@ typedef struct {
   double press_residual[8];/* final relative residual of each pressure solve          */
   double seconds;          /* wall time of the step                                   */
   double max_divergence;   /* max_i |Sum_j D_ij v_j| over unpinned tets after the step */
+  int fallbacks;           /* pressure solves that fell back to plain GMRES               */
 } stdg_step_stats;
 
 /* Velocity data kinds for initial and Dirichlet boundary values (evaluated on the device).
@@ -265,6 +268,10 @@ stdg_status stdg_gnn_loss_grad(stdg_solver* s, const double* R_dev, const double
  * (at most max_pairs in total, device memory sized on the first call). */
 stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b_dev, int nsnap, int every, int max_pairs,
                              int* total_pairs);
+/* While nsnap > 0, every pressure system that stdg_step solves is first passed to
+ * stdg_gnn_harvest(s, b, nsnap, every, max_pairs) (an extra solve per Picard iteration); nsnap = 0
+ * stops harvesting. */
+stdg_status stdg_gnn_autoharvest(stdg_solver* s, int nsnap, int every, int max_pairs);
 /* `epochs` passes of Adam (learning rate lr, `batch` pairs per update) over the harvested pairs. */
 stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int batch, double* first_loss,
                            double* last_loss);

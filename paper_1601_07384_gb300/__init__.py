@@ -179,7 +179,7 @@ class Solver:
         st = SolveStats()
         _lib.check(_lib.load().stdg_solve(self._h, _ptr(b), _ptr(x), float(tol), SOLVER[method], C.byref(st)))
         return x, {"iterations": st.iterations, "restarts": st.restarts, "rel_residual": st.rel_residual,
-                   "seconds": st.seconds}
+                   "seconds": st.seconds, "fallback": st.fallback}
 
     def solve_noalloc(self, b, x, tol=1e-10):
         """stdg_solve_noalloc: the Kronecker-decoupled CG solve without any device allocation
@@ -210,7 +210,7 @@ class Solver:
         k = st.picard
         return {"picard": k, "press_iters": list(st.press_iters[:k]), "visc_iters": list(st.visc_iters[:k]),
                 "press_residual": list(st.press_residual[:k]), "seconds": st.seconds,
-                "max_divergence": st.max_divergence}
+                "max_divergence": st.max_divergence, "fallbacks": st.fallbacks}
 
     def get_state(self):
         torch = _torch()
@@ -264,6 +264,9 @@ class Solver:
         _lib.check(_lib.load().stdg_gnn_harvest(self._h, _ptr(self._dev(b)), int(nsnap), int(every), int(max_pairs),
                                                 C.byref(tot)))
         return tot.value
+
+    def gnn_autoharvest(self, nsnap=8, every=50, max_pairs=64):
+        _lib.check(_lib.load().stdg_gnn_autoharvest(self._h, int(nsnap), int(every), int(max_pairs)))
 
     def gnn_train(self, epochs=50, lr=1e-3, batch=4):
         a = C.c_double(); b = C.c_double()

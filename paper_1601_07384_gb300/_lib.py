@@ -20,13 +20,13 @@ class StdgError(RuntimeError):
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("rel_residual", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("fallback", C.c_int)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("picard", C.c_int), ("press_iters", C.c_int * 8), ("visc_iters", C.c_int * 8),
                 ("press_residual", C.c_double * 8), ("seconds", C.c_double),
-                ("max_divergence", C.c_double)]
+                ("max_divergence", C.c_double), ("fallbacks", C.c_int)]
 
 
 class SolverOptions(C.Structure):
@@ -83,6 +83,7 @@ SIGNATURES = {
     "stdg_gnn_loss_grad": (C.c_int, [P, P, P, C.c_int, DP, C.POINTER(C.c_float)]),
     "stdg_gnn_harvest": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stdg_gnn_train": (C.c_int, [P, C.c_int, C.c_double, C.c_int, DP, DP]),
+    "stdg_gnn_autoharvest": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
     "stdg_profile_read": (C.c_int, [P, C.POINTER(ProfileStats)]),
     "stdg_last_error": (C.c_char_p, []),
     "stdg_version": (C.c_char_p, []),

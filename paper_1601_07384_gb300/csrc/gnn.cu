@@ -619,3 +619,9 @@ extern "C" stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b, int nsn
   if (cudaStreamSynchronize(S(s)) != cudaSuccess) { set_error("stdg_gnn_harvest: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
   return STDG_OK;
 }
+
+extern "C" stdg_status stdg_gnn_autoharvest(stdg_solver* s, int nsnap, int every, int max_pairs) {
+  if (!s || !s->gnn || nsnap < 0 || (nsnap > 0 && (every < 1 || max_pairs < 1))) { set_error("stdg_gnn_autoharvest: invalid argument"); return STDG_EINVAL; }
+  s->ah_nsnap = nsnap; s->ah_every = every; s->ah_max = max_pairs;
+  return STDG_OK;
+}

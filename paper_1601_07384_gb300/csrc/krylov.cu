@@ -115,6 +115,48 @@ __global__ void __launch_bounds__(128) k_bjacobi(int ne, int N, int Ng, const do
   }
 }
 
+// Same with binary32 inverses and binary32 products (the preconditioner need not be FP64; the
+// CG iterates, residuals and scalars stay binary64).
+__global__ void __launch_bounds__(256) k_bjacobi32(int ne, int N, int Ng, const float* __restrict__ Binv,
+                                                   const double* __restrict__ r, double* __restrict__ z,
+                                                   double* part) {
+  extern __shared__ float rsf[];
+  const int Nst = N * Ng;
+  const int TB = blockDim.x / Nst;
+  const size_t NN = (size_t)N * N;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int tl = threadIdx.x / Nst, o = threadIdx.x - tl * Nst, a = o / N, k = o - a * N;
+  for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TB * Nst; idx += blockDim.x) {
+      const int i = i0 + idx / Nst;
+      rsf[idx] = i < ne ? (float)r[(size_t)i0 * Nst + idx] : 0.0f;
+    }
+    __syncthreads();
+    const int i = i0 + tl;
+    if (tl < TB && i < ne) {
+      const float* B = Binv + (size_t)i * NN + k;
+      const float* rr = rsf + tl * Nst + a * N;
+      float sacc = 0.0f;
+      for (int l = 0; l < N; ++l) sacc = fmaf(B[(size_t)l * N], rr[l], sacc);
+      z[(size_t)i * Nst + o] = (double)sacc;
+      acc[a] = fma((double)sacc, r[(size_t)i * Nst + o], acc[a]);
+    }
+  }
+  __shared__ double red[8][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = 0; q < Ng; ++q) {
+    double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < Ng) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x][q];
+    part[(size_t)blockIdx.x * Ng + threadIdx.x] = t;
+  }
+}
+
 // beta_a = rznew_a / rz_a; rz <- rznew; res = sqrt(mix2)
 __global__ void k_cg_beta2(int Ng, double* rz, const double* rznew, double* beta, double* res, const double* mix2) {
   int a = threadIdx.x;
@@ -400,10 +442,13 @@ static stdg_status run_batched(stdg_solver* s, int B, int kernels_per_iter, int 
 
 static stdg_status ensure_block_inverse(stdg_solver* s) {
   if (s->Binv) return STDG_OK;
-  stdg_status e = dev_alloc(s, (void**)&s->Binv, (size_t)s->ne * s->N * s->N * sizeof(double));
+  const size_t cnt = (size_t)s->ne * s->N * s->N;
+  stdg_status e = dev_alloc(s, (void**)&s->Binv, cnt * sizeof(double));
   if (e != STDG_OK) return e;
-  ++s->nlaunch;
+  if ((e = dev_alloc(s, (void**)&s->lpBinv, cnt * sizeof(float))) != STDG_OK) return e;
+  s->nlaunch += 2;
   cudaError_t ce = launch_block_inverse((int)s->ne, s->N, s->Bdiag, s->Binv, s->stream);
+  if (ce == cudaSuccess) { lp_kernels().f32(s->stream, (int64_t)cnt, s->Binv, s->lpBinv); ce = cudaGetLastError(); }
   if (ce != cudaSuccess) { set_error("block inverse launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
   return STDG_OK;
 }
@@ -418,7 +463,9 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   double* r = s->kr; double* p = s->kp; double* q = s->kq; double* z = s->kz;
   double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
   double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
-  const size_t bj_smem = (size_t)s->Nst * sizeof(double);
+  const int bj_tb = s->Nst > 256 ? 1 : 256 / s->Nst;
+  const int bj_threads = bj_tb * s->Nst > 256 ? s->Nst : 256;
+  const size_t bj_smem = (size_t)bj_tb * s->Nst * sizeof(float);
   if (precond) {
     stdg_status e = ensure_block_inverse(s);
     if (e != STDG_OK) return e;
@@ -434,7 +481,7 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   }
   if (precond) {
     ++s->nlaunch;
-    k_bjacobi<<<kRedBlocks, 128, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->Binv, r, z, s->part);
+    k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
     cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   } else {
     cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
@@ -445,9 +492,11 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
   // one CG iteration; ends by copying the full-system residual norm to the host
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
-    if (evs) cudaEventRecord(evs[0], s->stream);
+    // inside a captured graph an event-record node only joins the dependency chain if later work
+    // waits on it, so each record is followed by a wait on the same event
+    if (evs) { cudaEventRecord(evs[0], s->stream); cudaStreamWaitEvent(s->stream, evs[0], 0); }
     stdg_status e = op_apply(s, op, p, q);
-    if (evs) cudaEventRecord(evs[1], s->stream);
+    if (evs) { cudaEventRecord(evs[1], s->stream); cudaStreamWaitEvent(s->stream, evs[1], 0); }
     if (e != STDG_OK) return e;
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
@@ -455,7 +504,7 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
     k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part);
     k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
     if (precond) {
-      k_bjacobi<<<kRedBlocks, 128, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->Binv, r, z, s->part);
+      k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
       k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
       k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
     } else {
@@ -679,11 +728,7 @@ static stdg_status ensure_lowprec(stdg_solver* s) {
   const size_t n = (size_t)s->ne * s->Nst;
   for (float** v : {&s->fr, &s->fp, &s->fq, &s->fz, &s->fx, &s->fb})
     if ((e = dev_alloc(s, (void**)v, n * sizeof(float))) != STDG_OK) return e;
-  if ((e = dev_alloc(s, (void**)&s->lpBinv, (size_t)s->ne * s->N * s->N * sizeof(float))) != STDG_OK) return e;
   if ((e = dev_alloc(s, (void**)&s->dmix, kMaxNg * kMaxNg * sizeof(double))) != STDG_OK) return e;
-  LpKernels lk = lp_kernels();
-  lk.f32(s->stream, (int64_t)s->ne * s->N * s->N, s->Binv, s->lpBinv);
-  ++s->nlaunch;
   cudaMemcpyAsync(s->dmix, s->K.data(), s->Ng * s->Ng * sizeof(double), cudaMemcpyHostToDevice, s->stream);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("low-precision setup failed"); return STDG_ECUDA; }
   return STDG_OK;
@@ -703,7 +748,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   for (int c = 0; c < Ng * Ng; ++c) Tp[c] = s->tm.Tp[c];
   double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
   double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
-  const double tau = 1e-4;
+  const double tau = 1e-5;
   cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   cudaMemcpyAsync(s->kr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   int total = 0, o = 0;
@@ -728,9 +773,9 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
     s->nlaunch += 3;
     auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
-      if (evs) cudaEventRecord(evs[0], s->stream);
+      if (evs) { cudaEventRecord(evs[0], s->stream); cudaStreamWaitEvent(s->stream, evs[0], 0); }
       cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
-      if (evs) cudaEventRecord(evs[1], s->stream);
+      if (evs) { cudaEventRecord(evs[1], s->stream); cudaStreamWaitEvent(s->stream, evs[1], 0); }
       if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
       lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
       k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
@@ -795,6 +840,7 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
   int it = 0, rs = 0;
   double rabs = 0.0;
   stdg_status r = STDG_OK;
+  if (st) st->fallback = 0;
   if (bn == 0.0) {
     cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   } else if (method == STDG_SOLVER_GMRES) {
@@ -805,6 +851,13 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
     if (r == STDG_OK)
       r = fgmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it, &rs, &rabs,
                  method == STDG_SOLVER_FGMRES_GNN ? 1 : 0);
+    if (method == STDG_SOLVER_FGMRES_GNN && (r == STDG_ENOCONV || r == STDG_ENAN)) {
+      // the learned preconditioner failed: plain GMRES (the paper's solver) produces the result
+      int it2 = 0, rs2 = 0;
+      r = gmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it2, &rs2, &rabs);
+      it += it2; rs += rs2;
+      if (st) st->fallback = 1;
+    }
   } else if ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG) &&
              (s->opt.precision == STDG_PREC_MIXED_F32 || s->opt.precision == STDG_PREC_MIXED_BF16)) {
     r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs);

@@ -174,7 +174,7 @@ struct TmaArgs {
 // x rows of the tets and their neighbours, all completing on the stage's "full" mbarrier.  The
 // consumer warps convert x, form the slot partial sums, release the stage on its "empty"
 // mbarrier and write y.  Consumers synchronise among themselves with a named barrier only.
-constexpr int kWsStages = 3;
+constexpr int kWsStages = 2;
 constexpr long kSpin = 20000;                    // bound on every mbarrier wait (x <= 1 ms suspend each)
 
 template <typename Pol, int NG>
@@ -299,29 +299,44 @@ __global__ void __launch_bounds__(416) k_apply_tma(TmaArgs<Pol> a, const typenam
     named_bar_sync(1, nct);
     if (computes) {
       const int r = my_tl * 5 + my_sl, k = my_k;
-      Acc acc[NG];
+      Acc acc[NG], acc2[NG];                    // two independent chains per column (even / odd terms)
 #pragma unroll
-      for (int q = 0; q < Ng; ++q) Pol::zero(acc[q]);
+      for (int q = 0; q < Ng; ++q) { Pol::zero(acc[q]); Pol::zero(acc2[q]); }
       const int2 t2 = tb[r];
       if (t2.x >= 0) {
         const TB* B = blkbuf + (size_t)st * rows * SB + (size_t)r * SB;
         const TZ* z = xs + (size_t)r * Nst;
         if (my_sl != 0 && t2.y) {
-          for (int l = 0; l < N; ++l) {            // A_lr^T row k = column k of A_lr
-            const TB b = B[(size_t)l * N + k];
+          int l = 0;
+          for (; l + 1 < N; l += 2) {              // A_lr^T row k = column k of A_lr
+            const TB b0 = B[(size_t)l * N + k], b1 = B[(size_t)(l + 1) * N + k];
 #pragma unroll
-            for (int q = 0; q < Ng; ++q) Pol::fma(acc[q], b, z[q * N + l]);
+            for (int q = 0; q < Ng; ++q) { Pol::fma(acc[q], b0, z[q * N + l]); Pol::fma(acc2[q], b1, z[q * N + l + 1]); }
+          }
+          if (l < N) {
+            const TB b0 = B[(size_t)l * N + k];
+#pragma unroll
+            for (int q = 0; q < Ng; ++q) Pol::fma(acc[q], b0, z[q * N + l]);
           }
         } else {
           const TB* Bk = B + (size_t)k * N;
-          int l = k;
-          for (int ll = 0; ll < N; ++ll) {         // row k walked from l = k (bank-conflict-free skew)
-            const TB b = Bk[l];
+          int l = k;                               // row k walked from l = k (bank-conflict-free skew)
+          int ll = 0;
+          for (; ll + 1 < N; ll += 2) {
+            const int l1 = (l + 1 == N) ? 0 : l + 1;
+            const TB b0 = Bk[l], b1 = Bk[l1];
 #pragma unroll
-            for (int q = 0; q < Ng; ++q) Pol::fma(acc[q], b, z[q * N + l]);
-            l = (l + 1 == N) ? 0 : l + 1;
+            for (int q = 0; q < Ng; ++q) { Pol::fma(acc[q], b0, z[q * N + l]); Pol::fma(acc2[q], b1, z[q * N + l1]); }
+            l = (l1 + 1 == N) ? 0 : l1 + 1;
+          }
+          if (ll < N) {
+            const TB b0 = Bk[l];
+#pragma unroll
+            for (int q = 0; q < Ng; ++q) Pol::fma(acc[q], b0, z[q * N + l]);
           }
         }
+#pragma unroll
+        for (int q = 0; q < Ng; ++q) Pol::add(acc[q], acc2[q]);
       }
 #pragma unroll
       for (int q = 0; q < Ng; ++q) part[((size_t)r * Ng + q) * N + k] = acc[q];
@@ -431,10 +446,11 @@ cudaError_t df_build_blocks(stdg_solver* s) {
   return cudaGetLastError();
 }
 
-// tets per stage: at most 384 consumer threads, and at most ~32 KB of blocks per stage
+// tets per stage: at most 384 consumer threads, and at most ~24 KB of blocks per stage (so that
+// several CTAs share an SM)
 int lp_tets_per_block(int N, size_t block_bytes) {
   int t = 384 / (5 * N);
-  const int tb = (int)(32768 / (5 * block_bytes));
+  const int tb = (int)(24576 / (5 * block_bytes));
   if (tb < t) t = tb;
   if (t < 1) t = 1;
   if (t > 16) t = 16;
@@ -566,23 +582,30 @@ __global__ void k_lp_cg_dir(int64_t n, int N, int Ng, const double* __restrict__
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     p[e] = fmaf((float)beta[(e / N) % Ng], p[e], z[e]);
 }
-__global__ void __launch_bounds__(128) k_lp_bjacobi(int ne, int N, int Ng, const float* __restrict__ Binv,
+// z_i = Binv_i r_i per time column, several tets per block pass (thread -> (tet, output)); partials of r.z
+__global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const float* __restrict__ Binv,
                                                     const float* __restrict__ r, float* __restrict__ z, double* part) {
   extern __shared__ float rs[];
   const int Nst = N * Ng;
+  const int TB = blockDim.x / Nst;                  // tets per pass
   const size_t NN = (size_t)N * N;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = blockIdx.x; i < ne; i += gridDim.x) {
+  const int tl = threadIdx.x / Nst, o = threadIdx.x - tl * Nst, a = o / N, k = o - a * N;
+  for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
     __syncthreads();
-    for (int o = threadIdx.x; o < Nst; o += blockDim.x) rs[o] = r[(size_t)i * Nst + o];
+    for (int idx = threadIdx.x; idx < TB * Nst; idx += blockDim.x) {
+      const int i = i0 + idx / Nst;
+      rs[idx] = i < ne ? r[(size_t)i0 * Nst + idx] : 0.0f;
+    }
     __syncthreads();
-    for (int o = threadIdx.x; o < Nst; o += blockDim.x) {
-      const int a = o / N, k = o % N;
-      const float* B = Binv + (size_t)i * NN + k;
-      float s = 0.0f;
-      for (int l = 0; l < N; ++l) s = fmaf(B[(size_t)l * N], rs[a * N + l], s);
-      z[(size_t)i * Nst + o] = s;
-      acc[a] += (double)(s * rs[o]);
+    const int i = i0 + tl;
+    if (tl < TB && i < ne) {
+      const float* B = Binv + (size_t)i * NN + k;   // symmetric: column k, coalesced over k
+      const float* rr = rs + tl * Nst + a * N;
+      float sacc = 0.0f;
+      for (int l = 0; l < N; ++l) sacc = fmaf(B[(size_t)l * N], rr[l], sacc);
+      z[(size_t)i * Nst + o] = sacc;
+      acc[a] += (double)(sacc * rs[tl * Nst + o]);
     }
   }
   __syncthreads();
@@ -626,7 +649,8 @@ LpKernels lp_kernels() {
     k_lp_cg_dir<<<kLpBlocks, 256, 0, st>>>(n, N, Ng, beta, z, p);
   };
   k.bjacobi = [](cudaStream_t st, int ne, int N, int Ng, const float* Binv, const float* r, float* z, double* part) {
-    k_lp_bjacobi<<<kLpBlocks, 128, N * Ng * sizeof(float), st>>>(ne, N, Ng, Binv, r, z, part);
+    const int Nst = N * Ng, TB = Nst > 256 ? 1 : 256 / Nst;
+    k_lp_bjacobi<<<kLpBlocks, TB * Nst > 256 ? Nst : 256, (size_t)TB * Nst * sizeof(float), st>>>(ne, N, Ng, Binv, r, z, part);
   };
   k.from64 = [](cudaStream_t st, int64_t ne, int N, int Ng, const double* Mdev, double coef, const double* in, float* out) {
     k_lp_from64<<<kLpBlocks, 256, 0, st>>>(ne, N, Ng, Mdev, coef, in, out);

@@ -71,6 +71,7 @@ struct stdg_solver {
   stdg::GnnState* gnn = nullptr;
   double* kzz = nullptr;                     // FGMRES preconditioned directions
   int snap_every = 0, snap_cap = 0, nsnap = 0;
+  int ah_nsnap = 0, ah_every = 0, ah_max = 0;   // harvest pairs from the pressure systems of stdg_step
   double* snaps = nullptr;
   // CUDA-graph batching of Krylov iterations
   cudaStream_t cstream = nullptr;

@@ -586,6 +586,11 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     if (launch_rhs(ne, N, Ng, s->dm.t2f, s->dm.left, s->Q, s->F, -s->dt, 1, s->bvec, st) != cudaSuccess) {
       set_error("rhs launch failed"); return STDG_ECUDA;
     }
+    if (s->gnn && s->ah_nsnap > 0) {
+      int tot = 0;
+      e = stdg_gnn_harvest(s, s->bvec, s->ah_nsnap, s->ah_every, s->ah_max, &tot);
+      if (e != STDG_OK) return e;
+    }
     stdg_solve_stats ss{};
     e = solve_pressure(s, s->bvec, s->dp, tol, method, &ss);
     if (e != STDG_OK) return e;
@@ -597,6 +602,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
       set_error("update launch failed"); return STDG_ECUDA;
     }
     local.press_iters[k] = ss.iterations;
+    local.fallbacks += ss.fallback;
     local.press_residual[k] = ss.rel_residual;
     local.visc_iters[k] = vits;
     local.picard = k + 1;
