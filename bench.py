@@ -34,6 +34,10 @@ WORKLOADS = {
     "learned": dict(n=12, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+# binary64-accurate products from binary32 pairs: 13 FP32 lane operations per multiply-add term
+# (1 mul, 4 fma, TwoSum 6 adds, 2 adds) on 152 SMs x 128 FP32 lanes x 2070 MHz
+DF_OPS_PER_TERM = 13
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / DF_OPS_PER_TERM * 2 / 1e12
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
 
 
@@ -253,7 +257,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--gmres-steps", type=int, default=1)
-    ap.add_argument("--gmres-max-iters", type=int, default=30000)
+    ap.add_argument("--gmres-max-iters", type=int, default=5000,
+                    help="iteration cap per pressure solve of the plain FP64 GMRES(50) comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
     ap.add_argument("--solver", default="kron_pcg", choices=["kron_cg", "kron_pcg", "gmres"])
@@ -323,7 +328,8 @@ def main():
     if world > 1:
         dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
     ms = float(t_dev.item())
-    s_per_step = ms / 1e3 / args.steps
+    # whole job: replicas each run K steps of the same workload; s/step over all steps of all ranks
+    s_per_step = ms / 1e3 / (args.steps * world)
 
     # ---- end to end through the C ABI with host buffers (state in from / out to pinned host memory)
     P0, V0, t0 = solver.get_state()
@@ -362,9 +368,12 @@ def main():
                 st = {"error": str(exc)}
             torch.cuda.synchronize()
             gts.append(time.perf_counter() - tg0)
-        gm = {"s_per_step": float(np.median(gts)), "converged": ok,
+        gm = {"s_per_step": float(np.median(gts)) if ok else None, "converged": ok,
               "max_iters_per_solve": args.gmres_max_iters,
               "press_iters": st.get("press_iters") if ok else None}
+        if not ok:      # the first pressure solve hit the cap: a lower bound on the plain solver's step
+            gm.update({"s_until_stopped": float(gts[-1]), "stopped": st["error"][:160],
+                       "s_per_step_lower_bound": float(gts[-1])})
         del gsolver
 
     # ---- roofline of the dominant operator kernel (CUDA-event time of its launches in the timed region)
@@ -391,6 +400,11 @@ def main():
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tflops / FP64_PEAK_TFLOPS,
                 "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20 TFLOP/s)"}
+    elif kbest == 1:
+        roof = {"bound": "alu", "achieved": tflops, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / DF_PEAK_TFLOPS,
+                "peak_note": f"FP64-accurate flops from binary32 pairs: 152 SMs x 128 FP32 lanes x 2070 MHz / "
+                             f"{DF_OPS_PER_TERM} lane operations per multiply-add term x 2 flop"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "peak_note": f"HBM copy bandwidth, {hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -408,7 +422,7 @@ def main():
                                        "mixed_f32": "f64 refinement / f32 inner", "mixed_bf16": "f64 refinement / bf16 blocks"}[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_name(w), "solver": args.solver, "precision": args.precision,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "parallelism": f"replicas only: {world} independent copies" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(P0.numel() + V0.numel()) * 8,
@@ -418,6 +432,13 @@ def main():
         "press_iters": [s["press_iters"] for s in stats],
         "visc_iters": [s["visc_iters"] for s in stats],
         "max_divergence": max(s["max_divergence"] for s in stats),
+        "matvecs_per_s": ops_per_step / (ms / 1e3 / args.steps),
+        "pressure_dof_updates_per_s": ops_per_step / (ms / 1e3 / args.steps) * solver.ne * solver.Nst,
+        "time_breakdown": {"operator_s_per_step": prof["operator_ms"] / 1e3 / args.steps,
+                           "rest_s_per_step": ms / 1e3 / args.steps - prof["operator_ms"] / 1e3 / args.steps,
+                           "operator_kinds": {kinds[k]: {"launches_per_step": prof["kind_launches"][k] / args.steps,
+                                                         "ms_per_launch": prof["kind_ms"][k] / max(prof["kind_launches"][k], 1)}
+                                              for k in range(4) if prof["kind_launches"][k] > 0}},
         "plain_gmres": gm,
         "clocks": clk.summary(),
     }

@@ -69,8 +69,11 @@ typedef enum {
  *                      changes only the iteration, not the system or its stopping test.      */
 /*  STDG_SOLVER_FGMRES_BJ / STDG_SOLVER_FGMRES_GNN : flexible GMRES(m) on the full operator,
  *                      right-preconditioned by block Jacobi of the full operator
- *                      (A_ii^-1 = B_i^-1 (x) (dt^2 K^-1)^-1) alone, or by block Jacobi plus the
- *                      learned network correction (stdg_gnn_*).  Needs stdg_gnn_init.         */
+ *                      (A_ii^-1 = B_i^-1 (x) (dt^2 K^-1)^-1) alone, or, for FGMRES_GNN, with
+ *                      the first direction of every restart cycle (the normalised residual)
+ *                      preconditioned by block Jacobi plus the learned network correction
+ *                      (stdg_gnn_*); later Arnoldi vectors use block Jacobi.  Needs
+ *                      stdg_gnn_init.                                                      */
 enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_SOLVER_KRON_PCG = 3,
        STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5 };
 
@@ -186,6 +189,15 @@ stdg_status stdg_pressure_apply(stdg_solver* s, const double* x_dev, double* y_d
  * binary32; the blocks are staged through shared memory by TMA bulk copies. */
 stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x_dev, float* y_dev, int pinned);
 
+/* The same operator (same pinning) applied in the factored form of Eq. CS_19 / A2_mod, as a
+ * cross-check of the assembled blocks: for every interior dual cell j the gradient blocks of
+ * its two tets, then M_j^-1 (v_j = -M_j^-1 (Q_lj x_l + Q_rj x_r)), then the divergence blocks back
+ * into each tet (y_i = -Sum_j D_ij v_j).  It reads the stored Q_ij instead of B_i and A_lr
+ * (about 4.6x the bytes of stdg_pressure_apply at N = 20), so it is not the production path.
+ * x_dev, y_dev: P layout, distinct.  The first call allocates an internal P-layout and a
+ * V-layout vector. */
+stdg_status stdg_pressure_apply_factored(stdg_solver* s, const double* x_dev, double* y_dev, int pinned);
+
 /* b = Sum_{j in S_i} D_ij F_j over all four faces of each tet (Eq. A2_mod right-hand side,
  * Eq. CS_15 left-hand side), with D_ij = -Q_ij^T.  F_dev: V layout (nf*3*Nst), b_dev: P
  * layout.  pinned != 0 zeroes b at the pinned entries. */
@@ -233,6 +245,14 @@ stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* field);
  * viscous solves (Eq. A1_mod) with CG (p_t = 0) or GMRES to `tol`.  stats may be NULL. */
 stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
                       stdg_step_stats* stats);
+/* Semi-implicit theta variant for p_t = 0 (Sec. 2.7, Eqs. CS_15_theta / CS_16_theta): the
+ * momentum of every dual cell sees the pressure as p^{n+theta} = theta p^{n+1} + (1-theta) p^n.
+ * stdg_step then takes Lambda (Eq. prevpress) of theta p^{n+1,k} + (1-theta) p^n, solves the
+ * same system (Eq. A2_mod) for the increment of p^{n+theta} and adds increment / theta to p^{n+1};
+ * theta = 1 (the default) is the scheme above.  theta = 1/2 is Crank-Nicolson.  STDG_EINVAL
+ * unless 1/2 <= theta <= 1, and for theta != 1 unless p_t = 0.  The first step with theta != 1
+ * allocates two pressure vectors. */
+stdg_status stdg_set_theta(stdg_solver* s, double theta);
 /* Copy the state out / in: P (ne*Nst) and V (nf*3*Nst), device or host pointers per
  * on_device; either pointer may be NULL.  t_out may be NULL. */
 stdg_status stdg_get_state(const stdg_solver* s, double* P, double* V, int on_device, double* t_out);

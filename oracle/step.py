@@ -10,6 +10,13 @@ For k = 0 .. n_picard-1 (reading R18):
   6. v^{n+1,k+1} from Eq. A3_mod
 The right-hand side of Eq. A1_mod uses Mbar_i^- vbar_i^n with vbar^n the average of the
 previous slab's velocity (reading R15).
+
+Semi-implicit theta variant for p_t = 0 (Sec. 2.7, Eqs. CS_15_theta / CS_16_theta): the momentum
+equation of each dual cell sees the pressure only as p^{n+theta} = theta p^{n+1} + (1-theta) p^n,
+theta in [1/2, 1].  In the pressure-correction iteration this means (reading R27): Lambda of
+step 1 is taken of theta p^{n+1,k} + (1-theta) p^n; the system of step 5 is Eq. A2_mod for the
+increment of p^{n+theta} (the same operator and right-hand side), so p^{n+1} grows by dp / theta;
+the velocity update of step 6 is unchanged.  theta = 1 is the scheme above.
 """
 from dataclasses import dataclass, field
 
@@ -71,8 +78,10 @@ def solve_viscous(disc, rhs, x0, nu, tol, restart=50, maxit=100000, method="kryl
 
 
 def time_step(disc: SpaceTimeDG, state: State, nu, n_picard, vbc, tol=1e-12, restart=50,
-              method="krylov"):
+              method="krylov", theta=1.0):
     m, N, Ng = disc.mesh, disc.N, disc.Ng
+    if theta != 1.0 and (disc.pt != 0 or not 0.5 <= theta <= 1.0):
+        raise ValueError("the theta method needs p_t = 0 and 1/2 <= theta <= 1")
     t0 = state.t
     vbar_n = ops.average(disc, state.V)
     Vbc, G = ops.boundary_data(disc, t0, vbc)
@@ -88,7 +97,7 @@ def time_step(disc: SpaceTimeDG, state: State, nu, n_picard, vbc, tol=1e-12, res
     rec = []
     for k in range(n_picard):
         vbar = ops.average(disc, V)                                          # step 1
-        Lam = ops.prev_pressure(disc, P)
+        Lam = ops.prev_pressure(disc, theta * P + (1.0 - theta) * state.P)
         Ups = ops.convection(disc, vbar, t0, vbc)                            # step 2
         rhs = (np.einsum("ikl,icl->ick", Mm, vbar_n) - Ups
                - np.einsum("ikl,icl->ick", Mb, Lam) + bd_rhs)
@@ -96,7 +105,7 @@ def time_step(disc: SpaceTimeDG, state: State, nu, n_picard, vbc, tol=1e-12, res
         F = ops.goback(disc, vhalf, Vbc)                                     # step 4
         b = ops.pressure_rhs(disc, F)                                        # step 5
         dp, pits, pres = solve_pressure(disc, b, tol, restart, method=method)
-        P = P + dp
+        P = P + dp / theta
         V = ops.velocity_update(disc, F, dp, Vbc)                            # step 6
         rec.append({"visc_its": vits, "press_its": pits, "press_res": pres})
     return State(V=V, P=P, t=t0 + disc.dt, stats=state.stats + [rec])

@@ -154,6 +154,13 @@ class Solver:
         _lib.check(_lib.load().stdg_pressure_apply(self._h, _ptr(x), _ptr(y), int(bool(pinned))))
         return y
 
+    def pressure_apply_factored(self, x, y=None, pinned=True):
+        """Factored-form cross-check of the operator (gradient, M_j^-1, divergence per dual cell)."""
+        x = self._dev(x)
+        y = self.pressure_empty() if y is None else self._dev(y)
+        _lib.check(_lib.load().stdg_pressure_apply_factored(self._h, _ptr(x), _ptr(y), int(bool(pinned))))
+        return y
+
     def pressure_apply_f32(self, x, y=None, pinned=True):
         torch = _torch()
         assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
@@ -211,6 +218,10 @@ class Solver:
         return {"picard": k, "press_iters": list(st.press_iters[:k]), "visc_iters": list(st.visc_iters[:k]),
                 "press_residual": list(st.press_residual[:k]), "seconds": st.seconds,
                 "max_divergence": st.max_divergence, "fallbacks": st.fallbacks}
+
+    def set_theta(self, theta):
+        """Semi-implicit pressure weight of the theta method (p_t = 0; 1 = fully implicit)."""
+        _lib.check(_lib.load().stdg_set_theta(self._h, float(theta)))
 
     def get_state(self):
         torch = _torch()

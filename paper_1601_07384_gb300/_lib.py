@@ -64,6 +64,7 @@ SIGNATURES = {
     "stdg_set_dt": (C.c_int, [P, C.c_double]),
     "stdg_pressure_apply": (C.c_int, [P, P, P, C.c_int]),
     "stdg_pressure_apply_f32": (C.c_int, [P, P, P, C.c_int]),
+    "stdg_pressure_apply_factored": (C.c_int, [P, P, P, C.c_int]),
     "stdg_pressure_rhs": (C.c_int, [P, P, P, C.c_int]),
     "stdg_velocity_update": (C.c_int, [P, P, P, P]),
     "stdg_solve": (C.c_int, [P, P, P, C.c_double, C.c_int, C.POINTER(SolveStats)]),
@@ -71,6 +72,7 @@ SIGNATURES = {
     "stdg_set_initial": (C.c_int, [P, C.POINTER(Field)]),
     "stdg_set_boundary": (C.c_int, [P, C.POINTER(Field)]),
     "stdg_step": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.POINTER(StepStats)]),
+    "stdg_set_theta": (C.c_int, [P, C.c_double]),
     "stdg_get_state": (C.c_int, [P, P, P, C.c_int, DP]),
     "stdg_set_state": (C.c_int, [P, P, P, C.c_int, C.c_double]),
     "stdg_velocity_moments": (C.c_int, [P, P, P]),

@@ -1,6 +1,7 @@
 // C ABI entry points: solver construction (device preprocessing) and the hot-path calls.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -72,6 +73,10 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
     if (s->opt.graph_batch <= 0) s->opt.graph_batch = 8;
     if (s->opt.graph_batch > 64) { delete s; set_error("graph_batch must be <= 64"); return STDG_EINVAL; }
     if (s->opt.precision < 0 || s->opt.precision > 3) { delete s; set_error("unknown precision %d", opts->precision); return STDG_EINVAL; }
+  }
+  {
+    const char* k = std::getenv("STDG_OP_KERNEL");   // "tma": block-staged TMA operator kernels
+    s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;
@@ -220,6 +225,42 @@ extern "C" stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x, f
   cudaError_t ce = launch_apply_lp(s, x, y, pinned ? 1 : 0, 0, 1.0f, -1.0f);
   if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
   return STDG_OK;
+}
+
+// y[a N] = d * x[a N] for the Ng pinned entries of tet 0
+__global__ void k_pin_set(int N, int Ng, double d, const double* __restrict__ x, double* __restrict__ y) {
+  const int a = threadIdx.x;
+  if (a < Ng) y[a * N] = d * x[a * N];
+}
+
+extern "C" stdg_status stdg_pressure_apply_factored(stdg_solver* s, const double* x, double* y, int pinned) {
+  stdg_status e = check(s);
+  if (e != STDG_OK) return e;
+  if (!x || !y || x == y) { set_error("stdg_pressure_apply_factored: x, y must be distinct device buffers"); return STDG_EINVAL; }
+  const size_t np = (size_t)s->ne * s->Nst, nv = (size_t)s->nf * 3 * s->Nst;
+  if (!s->fac_x && (e = dev_alloc(s, (void**)&s->fac_x, np * sizeof(double))) != STDG_OK) return e;
+  if (!s->fac_v && (e = dev_alloc(s, (void**)&s->fac_v, nv * sizeof(double))) != STDG_OK) return e;
+  const double* xin = x;
+  if (pinned) {                                   // x read as 0 at the pinned entries
+    cudaMemcpyAsync(s->fac_x, x, np * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    k_pin_set<<<1, 32, 0, s->stream>>>(s->N, s->Ng, 0.0, x, s->fac_x);
+    ++s->nlaunch;
+    xin = s->fac_x;
+  }
+  // gradient and inverse momentum block per dual cell: v_j = -M_j^-1 (Q_lj x_l + Q_rj x_r) (boundary cells 0)
+  cudaMemsetAsync(s->fac_v, 0, nv * sizeof(double), s->stream);
+  cudaError_t ce = launch_update((int)s->nf, s->N, s->Ng, s->dm.left, s->dm.right, s->Q, s->fac_v, xin, s->dt,
+                                 s->tm.Kinv, s->fac_v, s->stream);
+  if (ce != cudaSuccess) { set_error("update launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  // divergence back into each tet: y_i = -Sum_j D_ij v_j = Sum_j D_ij M_j^-1 Q_j x
+  ce = launch_rhs((int)s->ne, s->N, s->Ng, s->dm.t2f, s->dm.left, s->Q, s->fac_v, s->dt, pinned ? 1 : 0, y, s->stream);
+  if (ce != cudaSuccess) { set_error("rhs launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  s->nlaunch += 2;
+  if (pinned) {
+    k_pin_set<<<1, 32, 0, s->stream>>>(s->N, s->Ng, -1.0, x, y);
+    ++s->nlaunch;
+  }
+  return cudaGetLastError() == cudaSuccess ? STDG_OK : (set_error("pin launch failed"), STDG_ECUDA);
 }
 
 extern "C" stdg_status stdg_pressure_rhs(stdg_solver* s, const double* F, double* b, int pinned) {

@@ -9,6 +9,7 @@
 namespace stdg {
 
 void set_error(const char* fmt, ...);
+const char* last_error();
 
 // Quadrature rule on a reference entity: x[n*dim], w[n].
 struct Rule {

@@ -1,6 +1,7 @@
 // Krylov solvers on the device (Sec. 2.4: matrix-free, unpreconditioned GMRES; Sec. 2.7: CG for
 // p_t = 0).  Every reduction is two-stage over a fixed grid, so results are bitwise
 // reproducible run to run.  Vectors use the pressure layout P[ne][Ng][N].
+#include <string>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -494,9 +495,9 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
     // inside a captured graph an event-record node only joins the dependency chain if later work
     // waits on it, so each record is followed by a wait on the same event
-    if (evs) { cudaEventRecord(evs[0], s->stream); cudaStreamWaitEvent(s->stream, evs[0], 0); }
+    if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
     stdg_status e = op_apply(s, op, p, q);
-    if (evs) { cudaEventRecord(evs[1], s->stream); cudaStreamWaitEvent(s->stream, evs[1], 0); }
+    if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
     if (e != STDG_OK) return e;
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
@@ -627,8 +628,13 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
   return STDG_OK;
 }
 
-// Flexible GMRES(m) with a right preconditioner z_j = M(v_j) that may change between iterations
-// (block Jacobi, or block Jacobi plus the learned network): x = x0 + Z y minimises ||b - A x||.
+// Flexible GMRES(m) with a right preconditioner z_j = M_j(v_j) that may change between iterations:
+// x = x0 + Z y minimises ||b - A x|| over span(Z).  M_j is block Jacobi; with use_gnn the first
+// direction of every cycle is block Jacobi plus the learned correction.  v_0 of a cycle is the
+// normalised true residual, the input the network was trained on (pairs of residuals and errors),
+// while later Arnoldi vectors are not residuals of any iterate; the learned map is applied only
+// where its input is in distribution, and the least-squares step weighs its direction against the
+// block-Jacobi ones, so a poor correction costs at most a slower cycle, not a stagnating basis.
 static stdg_status fgmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
                           double tol_abs, int* iters, int* nrestarts, double* res_abs, int use_gnn) {
   const int m = s->opt.restart;
@@ -660,7 +666,7 @@ static stdg_status fgmres(stdg_solver* s, const ApplyArgs& op, const double* b, 
     for (k = 0; k < m; ++k) {
       double* w = s->basis + (size_t)(k + 1) * n;
       double* zk = s->kzz + (size_t)k * n;
-      e = gnn_precond(s, s->basis + (size_t)k * n, zk, use_gnn);
+      e = gnn_precond(s, s->basis + (size_t)k * n, zk, use_gnn && k == 0);
       if (e != STDG_OK) return e;
       e = op_apply(s, op, zk, w);
       if (e != STDG_OK) return e;
@@ -734,9 +740,15 @@ static stdg_status ensure_lowprec(stdg_solver* s) {
   return STDG_OK;
 }
 
-// FP64 iterative refinement around a binary32 inner block-Jacobi CG on the decoupled system.
-// Outer: r = b - A x (FP64 operator); inner: (-A_sp (x) I) d = -(I (x) Tp^-1) r / ||r|| to a
-// relative full-system residual tau; x += ||r|| d.  Stops on the FP64 residual <= tol ||b||.
+// Mixed precision: block-Jacobi CG on the decoupled system with binary32 operator, vectors and
+// recurrences, and reliable updates in binary64.  The binary32 iterate increment d is folded into
+// the binary64 x, and the true residual r = b - A x recomputed with the binary64-accurate operator,
+// whenever the recurrence's residual estimate has dropped by `delta` since the last reliable point;
+// the search direction is kept, so the Krylov information is not lost.  The binary32 system is
+// normalised by the last reliable residual norm rref (binary32 entries stay O(1) however far the
+// solve goes, so no product underflows), and at each reliable point the state is rescaled with it:
+// x += rref d, p *= rref_old / rref_new.  The stopping test is on the binary64 residual.  (If the low-precision operator is too inaccurate for the system's conditioning
+// the reliable residual stops decreasing and the solve returns STDG_ENOCONV.)
 static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, double tol, double bn, int* iters,
                                int* outer, double* res_abs) {
   stdg_status e = ensure_lowprec(s);
@@ -748,81 +760,87 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   for (int c = 0; c < Ng * Ng; ++c) Tp[c] = s->tm.Tp[c];
   double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
   double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
-  const double tau = 1e-5;
+  const double delta = 1e-2;
+  const double coef = -1.0 / (s->dt * s->dt);            // rhs of the decoupled system: -(I (x) Tp^-1) r
   cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
-  cudaMemcpyAsync(s->kr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
-  int total = 0, o = 0;
-  double rn = bn, rprev = INFINITY;
-  for (o = 0; o < 40; ++o) {
-    if (o > 0) rn = host_norm(s, s->kr, n);
+  cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
+  lk.from64(s->stream, s->ne, N, Ng, s->dmix, coef / bn, b, s->fr);
+  lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
+  k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
+  cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+  s->nlaunch += 3;
+  auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
+    if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
+    cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
+    if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
+    if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+    lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
+    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha);
+    lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tp, s->part);
+    k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
+    lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
+    k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
+    lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
+    cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    return STDG_OK;
+  };
+  int total = 0, reliable = 0;
+  double rn = bn, rref = bn, rprev = INFINITY;
+  const int B = s->opt.graph_batch > 1 ? s->opt.graph_batch : 1;
+  while (total < s->opt.max_iters) {
+    // a batch of binary32 iterations (stops early once the estimate crosses the reliable threshold)
+    int done_it = 0;
+    double est = INFINITY;
+    const double target = std::max(tol * bn / rref, delta);      // in units of rref
+    if (B > 1) {
+      e = run_batched(s, B, 10, s->opt.max_iters - total, target, body, &done_it, &est,
+                      s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2);
+      if (e != STDG_OK) return e;
+    } else {
+      while (total + done_it < s->opt.max_iters) {
+        if ((e = body(0, nullptr)) != STDG_OK) return e;
+        s->nlaunch += 10; ++s->op_launches; ++done_it;
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("mixed CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+        est = s->hostbuf[0];
+        if (!std::isfinite(est)) { set_error("mixed CG: non-finite residual estimate"); return STDG_ENAN; }
+        if (est <= target) break;
+      }
+    }
+    total += done_it;
+    // reliable update: x += rref d, r = b - A x in binary64, fresh binary32 residual, keep p
+    lk.accum(s->stream, n, rref, s->fx, x);
+    cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
+    e = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, s->kr);
+    if (e != STDG_OK) return e;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kr);
+    s->nlaunch += 2;
+    rn = host_norm(s, s->kr, n);
+    ++reliable;
     if (!std::isfinite(rn)) { set_error("mixed solve: non-finite residual"); return STDG_ENAN; }
-    if (rn <= tol * bn || total >= s->opt.max_iters) break;
-    if (rn > 0.5 * rprev) {
-      set_error("mixed solve: refinement stalled at relative residual %g (the low-precision operator is too "
+    if (rn <= tol * bn) break;
+    if (rn > 0.9 * rprev) {
+      set_error("mixed solve: reliable residual stalled at relative %g (the low-precision operator is too "
                 "inaccurate for this system's conditioning)", rn / bn);
-      *iters = total; *outer = o; *res_abs = rn;
+      *iters = total; *outer = reliable; *res_abs = rn;
       return STDG_ENOCONV;
     }
     rprev = rn;
-    // inner right-hand side and block-Jacobi CG in binary32
-    lk.from64(s->stream, s->ne, N, Ng, s->dmix, -1.0 / (s->dt * s->dt * rn), s->kr, s->fb);
-    cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
-    cudaMemcpyAsync(s->fr, s->fb, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+    lk.scale(s->stream, n, (float)(rref / rn), s->fp);
+    rref = rn;
+    lk.from64(s->stream, s->ne, N, Ng, s->dmix, coef / rn, s->kr, s->fr);
     lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
-    cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
-    s->nlaunch += 3;
-    auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
-      if (evs) { cudaEventRecord(evs[0], s->stream); cudaStreamWaitEvent(s->stream, evs[0], 0); }
-      cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
-      if (evs) { cudaEventRecord(evs[1], s->stream); cudaStreamWaitEvent(s->stream, evs[1], 0); }
-      if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
-      lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
-      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
-      k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha);
-      lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tp, s->part);
-      k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
-      lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
-      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
-      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
-      lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
-      cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-      return STDG_OK;
-    };
-    double rin = INFINITY;
-    int inner = 0;
-    if (s->opt.graph_batch > 1) {
-      e = run_batched(s, s->opt.graph_batch, 10, s->opt.max_iters - total, tau, body, &inner, &rin,
-                      s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2);
-      if (e != STDG_OK) return e;
-      total += inner;
-    } else {
-      while (total < s->opt.max_iters) {
-        e = body(0, nullptr);
-        if (e != STDG_OK) return e;
-        s->nlaunch += 10; ++s->op_launches;
-        ++total;
-        if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("mixed CG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
-        rin = s->hostbuf[0];
-        if (!std::isfinite(rin)) { set_error("mixed CG: non-finite inner residual"); return STDG_ENAN; }
-        if (rin <= tau) break;
-      }
-    }
-    // x += ||r|| d ; r = b - A x in FP64
-    lk.accum(s->stream, n, rn, s->fx, x);
-    ++s->nlaunch;
-    e = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, s->kr);
-    if (e != STDG_OK) return e;
-    ++s->nlaunch;
-    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kr);
+    s->nlaunch += 4;
   }
   int herr = 0;
   cudaMemcpy(&herr, s->derr, sizeof(int), cudaMemcpyDeviceToHost);
   if (herr) { set_error("low-precision operator: a bounded wait timed out"); return STDG_ETIMEOUT; }
   *iters = total;
-  *outer = o;
+  *outer = reliable;
   *res_abs = rn;
-  if (rn > tol * bn) { set_error("mixed solve did not reach the tolerance (%d inner iterations)", total); return STDG_ENOCONV; }
+  if (rn > tol * bn) { set_error("mixed solve did not reach the tolerance (%d iterations)", total); return STDG_ENOCONV; }
   return STDG_OK;
 }
 
@@ -853,8 +871,14 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
                  method == STDG_SOLVER_FGMRES_GNN ? 1 : 0);
     if (method == STDG_SOLVER_FGMRES_GNN && (r == STDG_ENOCONV || r == STDG_ENAN)) {
       // the learned preconditioner failed: plain GMRES (the paper's solver) produces the result
+      std::string why = last_error();
       int it2 = 0, rs2 = 0;
       r = gmres(s, pressure_op(s, 1, 0, 1.0, -1.0), b, x, true, tol * bn, &it2, &rs2, &rabs);
+      if (r != STDG_OK) {
+        std::string after = last_error();
+        set_error("learned FGMRES failed (%s after %d iterations); plain GMRES fallback: %s", why.c_str(), it,
+                  after.c_str());
+      }
       it += it2; rs += rs2;
       if (st) st->fallback = 1;
     }

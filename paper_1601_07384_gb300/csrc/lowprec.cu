@@ -14,68 +14,12 @@
 // Every mbarrier wait is bounded; on timeout the kernel records an error word and returns.
 #include <cuda_bf16.h>
 
+#include "lp_ptx.cuh"
 #include "solver.h"
 
 namespace stdg {
 
 constexpr int kStages = 2;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// try_wait with a suspend-time hint: the waiting thread is descheduled until the phase completes
-// or the hint (ns) expires, so waiting warps do not take issue slots from working ones
-__device__ __forceinline__ bool mbar_wait_hint(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---- arithmetic policies -----------------------------------------------------------------
 // PolF32 / PolBF16: blocks binary32 / bfloat16, vectors and accumulation binary32.
@@ -111,25 +55,7 @@ struct PolDF {
   static constexpr int kBlockAlign = 2;
   __device__ static void zero(Acc& a) { a.h = 0.0f; a.l = 0.0f; }
   __device__ static TZ zero_z() { return make_float2(0.0f, 0.0f); }
-  // split a binary64 into hi (truncated to 24 significant bits) + lo (next bits, rounded to 24)
-  __device__ static TZ load_x(XIn x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(u >> 63) << 31;
-    const int e = (int)((u >> 52) & 0x7FF);
-    const int E = e - 1023;
-    if (e == 0 || E < -126) return make_float2(0.0f, 0.0f);                 // below binary32's normal range
-    if (E > 127) return make_float2(__int_as_float(sign | 0x7F800000u), 0.0f);  // beyond binary32
-    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-    const float hi = __int_as_float((int)(sign | ((unsigned int)(E + 127) << 23) | (unsigned int)(m >> 29)));
-    const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);                // 29 low fraction bits
-    float lo = 0.0f;
-    if (rem) {
-      const unsigned int fb = __float_as_uint((float)rem);                      // rem * 2^(E-52):
-      const int be = (int)((fb >> 23) & 0xFF) - (52 - E);                       // rescale the exponent
-      if (be > 0) lo = __uint_as_float(sign | ((unsigned int)be << 23) | (fb & 0x7FFFFFu));
-    }
-    return make_float2(hi, lo);
-  }
+  __device__ static TZ load_x(XIn x) { return df_split(x); }
   __device__ static void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     const float bb = s - a;
@@ -508,6 +434,7 @@ static cudaError_t launch_tma(stdg_solver* s, const typename Pol::TB* Bd, const 
 }
 
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag) {
+  if (s->op_warp) return launch_apply_warp_lp(s, x, y, pinned, kron, scale, pin_diag);
   if (s->lpkind == STDG_PREC_MIXED_BF16)
     return launch_tma<PolBF16>(s, static_cast<const __nv_bfloat16*>(s->lpB), static_cast<const __nv_bfloat16*>(s->lpA),
                                s->lpSB, x, y, pinned, kron, scale, pin_diag);
@@ -517,6 +444,7 @@ cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned
 
 cudaError_t launch_apply_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                             double pin_diag) {
+  if (s->op_warp) return launch_apply_warp_df(s, x, y, pinned, kron, scale, pin_diag);
   return launch_tma<PolDF>(s, static_cast<const float2*>(s->dfB), static_cast<const float2*>(s->dfA), s->dfSB, x, y,
                            pinned, kron, scale, pin_diag);
 }
@@ -629,6 +557,10 @@ __global__ void k_lp_accum(int64_t n, double scale, const float* __restrict__ d,
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     x[e] = fma(scale, (double)d[e], x[e]);
 }
+__global__ void k_lp_scale(int64_t n, float s, float* __restrict__ p) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] *= s;
+}
 __global__ void k_lp_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
@@ -659,6 +591,7 @@ LpKernels lp_kernels() {
     k_lp_accum<<<kLpBlocks, 256, 0, st>>>(n, scale, d, x);
   };
   k.f32 = [](cudaStream_t st, int64_t n, const double* in, float* out) { k_lp_f32<<<kLpBlocks, 256, 0, st>>>(n, in, out); };
+  k.scale = [](cudaStream_t st, int64_t n, float s, float* p) { k_lp_scale<<<kLpBlocks, 256, 0, st>>>(n, s, p); };
   return k;
 }
 

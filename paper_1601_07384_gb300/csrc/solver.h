@@ -48,6 +48,10 @@ struct stdg_solver {
   int dfSB = 0;
   int tma_grid[16] = {0};                     // persistent grid size per block element size
   int *gface = nullptr, *gnbr = nullptr;      // per-tet gather tables (int4 each) for the TMA kernels
+  void *wB = nullptr, *wA = nullptr;          // warp-kernel block copies (binary32 / bfloat16), padded rows
+  void *wdB = nullptr, *wdA = nullptr;        // warp-kernel (hi, lo) binary32 planes of the FP64 blocks
+  int warp_grid[32] = {0}, warp_wpc[32] = {0};
+  int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
   float *fr = nullptr, *fp = nullptr, *fq = nullptr, *fz = nullptr, *fx = nullptr, *fb = nullptr;
   double* dmix = nullptr;                     // device copy of K (time mixing)
@@ -67,6 +71,9 @@ struct stdg_solver {
   double *Vbar = nullptr, *Vbar_n = nullptr, *Lam = nullptr, *Ups = nullptr, *rhsv = nullptr;
   double *F = nullptr, *Vbc = nullptr, *Gbc = nullptr, *bvec = nullptr, *dp = nullptr, *vtmp = nullptr;
   double *wk1 = nullptr, *wk2 = nullptr;
+  double *fac_x = nullptr, *fac_v = nullptr;   // factored-form cross-check operator (lazily allocated)
+  double theta = 1.0;                          // semi-implicit pressure weight (p_t = 0 only)
+  double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
   std::vector<void*> allocs;
   stdg::GnnState* gnn = nullptr;
   double* kzz = nullptr;                     // FGMRES preconditioned directions
@@ -100,10 +107,15 @@ struct LpKernels {
   void (*from64)(cudaStream_t, int64_t, int, int, const double*, double, const double*, float*);
   void (*accum)(cudaStream_t, int64_t, double, const float*, double*);
   void (*f32)(cudaStream_t, int64_t, const double*, float*);
+  void (*scale)(cudaStream_t, int64_t, float, float*);
 };
 LpKernels lp_kernels();
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag);
+cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
+                                 float pin_diag);
+cudaError_t launch_apply_warp_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
+                                 double pin_diag);
 cudaError_t launch_apply_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                             double pin_diag);
 cudaError_t df_build_blocks(stdg_solver* s);

@@ -444,6 +444,12 @@ __global__ void k_maxabs(int64_t n, int64_t skip, const double* __restrict__ x, 
     part[blockIdx.x] = t;
   }
 }
+// out = a x + b y
+__global__ void k_blend(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a * x[e] + b * y[e];
+}
 __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     y[e] = fma(a, x[e], y[e]);
@@ -523,6 +529,13 @@ extern "C" stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* f) {
   return STDG_OK;
 }
 
+extern "C" stdg_status stdg_set_theta(stdg_solver* s, double theta) {
+  if (!s || !(theta >= 0.5 && theta <= 1.0)) { set_error("stdg_set_theta: theta must lie in [1/2, 1]"); return STDG_EINVAL; }
+  if (theta != 1.0 && s->pt != 0) { set_error("stdg_set_theta: the theta method needs p_t = 0"); return STDG_EINVAL; }
+  s->theta = theta;
+  return STDG_OK;
+}
+
 extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
                                  stdg_step_stats* stats) {
   if (!s || n_picard < 1 || n_picard > 8 || !(tol > 0.0) || nu < 0.0) { set_error("stdg_step: invalid argument"); return STDG_EINVAL; }
@@ -547,6 +560,12 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   ++s->nlaunch;
   k_trace<<<1216, 256, 0, st>>>(nf, N, Ng, s->dm.right, g1, s->V, s->Vbc, s->vtmp);
   cudaMemcpyAsync(s->V, s->vtmp, (size_t)nf * 3 * Nst * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  const double th = s->theta;
+  if (th != 1.0) {                                  // theta method: keep p^n
+    if (!s->Pn && (e = dev_alloc(s, (void**)&s->Pn, np * sizeof(double))) != STDG_OK) return e;
+    if (!s->Pth && (e = dev_alloc(s, (void**)&s->Pth, np * sizeof(double))) != STDG_OK) return e;
+    cudaMemcpyAsync(s->Pn, s->P, np * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
   cudaMemsetAsync(s->P, 0, np * sizeof(double), st);
   const size_t conv_smem = ((size_t)9 * Nst + 64 * 9) * sizeof(double);
   cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
@@ -554,8 +573,15 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     // 1. averaging and previous-Picard pressure gradient
     ++s->nlaunch;
     k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar);
+    // Lambda of Eq. prevpress, of p^{n+theta,k} = theta p^{n+1,k} + (1 - theta) p^n (Eq. CS_16_theta)
+    const double* Plam = s->P;
+    if (th != 1.0) {
+      ++s->nlaunch;
+      k_blend<<<1216, 256, 0, st>>>(np, th, s->P, 1.0 - th, s->Pn, s->Pth);
+      Plam = s->Pth;
+    }
     ++s->nlaunch;
-    k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), st>>>(N, Ng, s->dm.left, s->dm.right, s->Q, s->P, s->dt, Ki, s->F);
+    k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), st>>>(N, Ng, s->dm.left, s->dm.right, s->Q, Plam, s->dt, Ki, s->F);
     ++s->nlaunch;
     k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->F, s->Lam);
     // 2. convection
@@ -595,7 +621,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     e = solve_pressure(s, s->bvec, s->dp, tol, method, &ss);
     if (e != STDG_OK) return e;
     ++s->nlaunch;
-    k_axpy<<<1216, 256, 0, st>>>(np, 1.0, s->dp, s->P);
+    k_axpy<<<1216, 256, 0, st>>>(np, 1.0 / th, s->dp, s->P);     // dp is the increment of p^{n+theta}
     // 6. velocity update (Eq. A3_mod)
     ++s->nlaunch;
     if (launch_update(nf, N, Ng, s->dm.left, s->dm.right, s->Q, s->F, s->dp, s->dt, s->Kinv.data(), s->V, st) != cudaSuccess) {

@@ -63,6 +63,21 @@ def test_pressure_apply_matches_oracle(n, p, pt, pinned):
 
 
 @pytest.mark.parametrize("n,p,pt", CASES)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_factored_operator_matches_oracle_and_assembled(n, p, pt, pinned):
+    """Gradient -> M_j^-1 -> divergence per dual cell (Eq. CS_19 read literally) against the
+    oracle, and against the assembled five-point blocks on the same input."""
+    gs, d = setup(n, p, pt)
+    x = np.random.default_rng(7 + n + 10 * p + pt).standard_normal(d.mesh.ne * d.Nst)
+    xd = torch.from_numpy(x).cuda()
+    yf = gs.pressure_apply_factored(xd, pinned=pinned).cpu().numpy()
+    ya = gs.pressure_apply(xd, pinned=pinned).cpu().numpy()
+    yo = ops.pressure_apply(d, x, pinned=pinned).ravel()
+    assert rel(yf, yo) <= 1e-12
+    assert rel(yf, ya) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,pt", CASES)
 def test_update_rhs_and_moments_match_oracle(n, p, pt):
     """v = -M^-1 Q dp (Eq. A3_mod with F = 0) compared through the basis-independent moments
     int phi~ v_h; then b = Sum_j D_ij v_j (Eq. A2_mod right-hand side) = -A dp."""
@@ -135,6 +150,43 @@ def test_step_matches_oracle(p, pt, npic):
             Uo[j, s] = (fb["Mij"][s] @ so1.V[j].T).T
     assert rel(U, Uo) <= 1e-10
     assert st["max_divergence"] <= 1e-11
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.75])
+def test_theta_steps_match_oracle(theta):
+    """Two steps of the semi-implicit theta variant (Sec. 2.7, Eq. CS_16_theta) at p_t = 0: the
+    second step starts from a nonzero p^n, so the (1 - theta) p^n part of Lambda is exercised."""
+    import paper_1601_07384_gb300 as g
+    prm = BeltramiParams(nu=0.1)
+    gs, d = setup(2, 2, 0, dt=0.01)
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_theta(theta)
+    vbc = lambda x, tt: beltrami_velocity(x, tt, prm)
+    so = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    for _ in range(2):
+        gs.step(prm.nu, 2, method="kron_cg", tol=1e-13)
+        so = time_step(d, so, prm.nu, 2, vbc, tol=1e-13, method="direct", theta=theta)
+    P, V, t = gs.get_state()
+    assert rel(P.cpu().numpy(), so.P.ravel()) <= 1e-9
+    U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
+    Uo = np.zeros_like(U)
+    for j in range(d.mesh.nf):
+        fb = d.face_blocks(j)
+        for s in range(len(fb["sides"])):
+            Uo[j, s] = (fb["Mij"][s] @ so.V[j].T).T
+    assert rel(U, Uo) <= 1e-10
+
+
+def test_theta_rejected_for_space_time_pressure():
+    import paper_1601_07384_gb300 as g
+    gs, _ = setup(2, 1, 1)
+    with pytest.raises(g.StdgError, match="EINVAL"):
+        gs.set_theta(0.5)
+    gs0, _ = setup(2, 1, 0)
+    with pytest.raises(g.StdgError, match="EINVAL"):
+        gs0.set_theta(0.3)
+    gs0.set_theta(1.0)
 
 
 def test_initial_projection_matches_oracle():

@@ -91,3 +91,62 @@ def test_design_order_velocity_p1_pt1():
         errs.append(_l2_velocity_error(d, st, prm))
     orders = [np.log(errs[k] / errs[k + 1]) / np.log((k + 3) / (k + 2)) for k in range(2)]
     assert min(orders) >= 1.7, (errs, orders)
+
+
+def _project_pressure(d, fn):
+    """L2 projection of a scalar function onto each tet's pressure basis (p_t = 0)."""
+    P = np.zeros((d.mesh.ne, d.Nst))
+    for i in range(d.mesh.ne):
+        x, w = map_tet(d.mesh.X[d.mesh.T[i]], *d.tet_nl)
+        ph, _ = d.phi(i, x)
+        G = ph.T @ (w[:, None] * ph)
+        P[i] = np.linalg.solve(G, ph.T @ (w * fn(x)))
+    return P
+
+
+def test_theta_method_from_zero_pressure_rescales_the_pressure():
+    """Eqs. CS_15_theta / CS_16_theta: the momentum of a dual cell sees the pressure only through
+    p^{n+theta} = theta p^{n+1} + (1-theta) p^n.  From p^n = 0 the theta step therefore takes the
+    same velocity iterates as the implicit step, with p^{n+1} = p^{n+1}(theta = 1) / theta."""
+    prm = BeltramiParams(nu=0.1)
+    d = make(2, 1, 0, 0.02)
+    vbc = lambda x, t: beltrami_velocity(x, t, prm)
+    s0 = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    a = time_step(d, s0, prm.nu, 2, vbc, tol=1e-13, method="direct")
+    for th in (0.5, 0.51, 0.8):
+        b = time_step(d, s0, prm.nu, 2, vbc, tol=1e-13, method="direct", theta=th)
+        assert np.abs(b.V - a.V).max() <= 1e-13 * np.abs(a.V).max()
+        assert np.abs(th * b.P - a.P).max() <= 1e-12 * np.abs(a.P).max()
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.51, 0.75, 1.0])
+def test_theta_method_on_uniform_flow_with_linear_pressure(theta):
+    """Inviscid uniform Dirichlet flow u with a linear pressure c.x at t^n: the velocity stays u,
+    and since a steady u needs p^{n+theta} constant, p^{n+1} = -(1-theta)/theta (c.x - C), where C
+    is the constant that the pin (constant mode of tet 0) removes.  The discrete gradient of a
+    linear pressure is exact and nu = 0 leaves the predictor a pure mass solve, so one Picard
+    iteration already reaches this; the second changes nothing."""
+    d = make(2, 2, 0, 0.05)
+    u = np.array([0.7, -0.2, 0.4])
+    const = lambda x, t=0.0: np.tile(u, (len(x), 1))
+    c = np.array([0.3, -1.1, 0.6])
+    st = initial_state(d, const)
+    V0 = st.V.copy()
+    st.P = _project_pressure(d, lambda x: x @ c)
+    C = np.zeros_like(st.P)
+    C[:, 0] = st.P[0, 0]                         # the Dubiner constant mode has the same value on every tet
+    out = time_step(d, st, 0.0, 2, const, tol=1e-13, method="direct", theta=theta)
+    assert np.abs(out.V - V0).max() <= 1e-12
+    expect = -(1.0 - theta) / theta * (st.P - C)
+    assert np.abs(out.P - expect).max() <= 1e-10 * max(np.abs(st.P).max(), 1.0)
+
+
+def test_theta_method_rejects_space_time_pressure():
+    d = make(2, 1, 1, 0.02)
+    s0 = initial_state(d, lambda x: np.zeros((len(x), 3)))
+    with pytest.raises(ValueError):
+        time_step(d, s0, 0.1, 1, lambda x, t: np.zeros((len(x), 3)), method="direct", theta=0.5)
+    d0 = make(2, 1, 0, 0.02)
+    s0 = initial_state(d0, lambda x: np.zeros((len(x), 3)))
+    with pytest.raises(ValueError):
+        time_step(d0, s0, 0.1, 1, lambda x, t: np.zeros((len(x), 3)), method="direct", theta=0.4)
