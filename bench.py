@@ -34,9 +34,9 @@ WORKLOADS = {
     "learned": dict(n=12, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
-# binary64-accurate products from binary32 pairs: 13 FP32 lane operations per multiply-add term
-# (1 mul, 4 fma, TwoSum 6 adds, 2 adds) on 152 SMs x 128 FP32 lanes x 2070 MHz
-DF_OPS_PER_TERM = 13
+# binary64-accurate products from binary32 pairs: 12 FP32 lane operations per multiply-add term
+# (1 mul, 3 fma, TwoSum 6 adds, 2 adds) on 152 SMs x 128 FP32 lanes x 2070 MHz
+DF_OPS_PER_TERM = 12
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / DF_OPS_PER_TERM * 2 / 1e12
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
 
@@ -377,8 +377,8 @@ def main():
         del gsolver
 
     # ---- roofline of the dominant operator kernel (CUDA-event time of its launches in the timed region)
-    kinds = ["fp64 blocks (k_apply)", "fp32-pair blocks (k_apply_tma<PolDF>)", "fp32 blocks (k_apply_tma<PolF32>)",
-             "bf16 blocks (k_apply_tma<PolBF16>)"]
+    kinds = ["fp64 blocks (k_apply)", "binary32-pair blocks (k_apply_warp<WDF>)", "binary32 blocks (k_apply_warp<WF32>)",
+             "bfloat16 blocks (k_apply_warp<WBF16>)"]
     kbest = int(np.argmax(prof["kind_ms"]))
     nlaunch_k = max(prof["kind_launches"][kbest], 1)
     op_launch_ms = prof["kind_ms"][kbest] / nlaunch_k
@@ -419,7 +419,7 @@ def main():
         "metric": METRIC, "value": s_per_step * 1.0, "unit": "s/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s_per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "df32": "f64 (products from fp32 pairs)",
-                                       "mixed_f32": "f64 refinement / f32 inner", "mixed_bf16": "f64 refinement / bf16 blocks"}[args.precision],
+                                       "mixed_f32": "f64 outer (pair products) / f32 inner", "mixed_bf16": "f64 outer (pair products) / bf16 inner"}[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_name(w), "solver": args.solver, "precision": args.precision,
                    "parallelism": f"replicas only: {world} independent copies" if world > 1 else "single GPU",

@@ -82,12 +82,16 @@ enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_
  *  STDG_PREC_DF32   : binary64 blocks and vectors, products formed in pairs of binary32
  *                     ("double-float", ~48-bit significand) because sm_103a's binary64
  *                     pipe is ~1/58 of its binary32 rate; results agree with STDG_PREC_FP64
- *                     to ~1e-14 relative per operator application.
- *  STDG_PREC_MIXED_F32 / STDG_PREC_MIXED_BF16 : the Kronecker CG methods run as FP64 iterative
- *                     refinement around an inner block-Jacobi CG whose operator blocks are
- *                     binary32 / bfloat16 (vectors and accumulation binary32); the outer
- *                     residual, the correction and the stopping test are binary64, so the
- *                     returned x meets the same FP64 residual tolerance.                   */
+ *                     to ~1e-14 relative per operator application.  Used for the pressure and
+ *                     the viscous operators inside the solves.
+ *  STDG_PREC_MIXED_F32 / STDG_PREC_MIXED_BF16 : the Kronecker CG methods run as an inner-outer
+ *                     iteration: flexible CG in binary64 (operator as in STDG_PREC_DF32)
+ *                     preconditioned by a fixed number of block-Jacobi CG iterations whose
+ *                     operator blocks are binary32 / bfloat16 (vectors and accumulation
+ *                     binary32).  Residual recurrence, scalars and stopping test are binary64,
+ *                     so the returned x meets the same FP64 residual tolerance; the viscous
+ *                     solves use the STDG_PREC_DF32 operator.  stdg_solve_stats.iterations
+ *                     counts the binary32 iterations and .restarts the outer ones.          */
 enum { STDG_PREC_FP64 = 0, STDG_PREC_DF32 = 1, STDG_PREC_MIXED_F32 = 2, STDG_PREC_MIXED_BF16 = 3 };
 
 typedef struct {
@@ -186,7 +190,7 @@ stdg_status stdg_pressure_apply(stdg_solver* s, const double* x_dev, double* y_d
 /* The same operator with binary32 vectors x_dev, y_dev (P layout, ne*Nst floats) and the
  * solver's low-precision blocks (binary32 or bfloat16 per its precision option, built on first
  * use; needs STDG_PREC_MIXED_F32 or STDG_PREC_MIXED_BF16, else STDG_EINVAL).  Accumulation is
- * binary32; the blocks are staged through shared memory by TMA bulk copies. */
+ * binary32; each warp stages its tet's blocks into shared memory with TMA bulk copies. */
 stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x_dev, float* y_dev, int pinned);
 
 /* The same operator (same pinning) applied in the factored form of Eq. CS_19 / A2_mod, as a

@@ -77,6 +77,8 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   {
     const char* k = std::getenv("STDG_OP_KERNEL");   // "tma": block-staged TMA operator kernels
     s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
+    const char* mi = std::getenv("STDG_MIXED_INNER");   // binary32 iterations per outer mixed step
+    if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = std::atoi(mi);
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;
@@ -166,7 +168,8 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   for (size_t k = 0; k < ex.size(); ++k) mi.e[k] = (unsigned char)ex[k];
   cudaError_t ce = launch_face_blocks(d, t, s->p, s->N, r->nq_lin, r->nqf_lin, mi, s->Q, s->Mij, s->C, s->x0h, s->stream);
   if (ce == cudaSuccess) ce = launch_assemble(d, s->N, s->Q, s->Aoff, s->Bdiag, s->Bvisc, s->stream);
-  if (ce == cudaSuccess && s->opt.precision == STDG_PREC_DF32) ce = df_build_blocks(s);
+  if (ce == cudaSuccess && s->opt.precision != STDG_PREC_FP64)      // pair blocks: DF32, and the mixed modes' outer operator
+    ce = s->op_warp ? warp_prepare(s, STDG_PREC_DF32) : df_build_blocks(s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) {
     set_error("device preprocessing failed: %s", cudaGetErrorString(ce));
@@ -216,8 +219,10 @@ extern "C" stdg_status stdg_pressure_apply_f32(stdg_solver* s, const float* x, f
     set_error("stdg_pressure_apply_f32 needs a solver created with STDG_PREC_MIXED_F32 or _BF16");
     return STDG_EINVAL;
   }
-  if (!s->lpB) {
-    cudaError_t ce = lp_build_blocks(s, s->opt.precision);
+  if (!s->lpB && !s->wB) {
+    cudaError_t ce;
+    if (s->op_warp) { s->lpkind = s->opt.precision; ce = warp_prepare(s, s->opt.precision); }
+    else ce = lp_build_blocks(s, s->opt.precision);
     s->nlaunch += 2;
     if (ce != cudaSuccess) { set_error("low-precision block copies failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
   }

@@ -561,6 +561,10 @@ __global__ void k_lp_scale(int64_t n, float s, float* __restrict__ p) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     p[e] *= s;
 }
+__global__ void k_lp_f32s(int64_t n, double sc, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)(sc * in[e]);
+}
 __global__ void k_lp_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
@@ -592,6 +596,9 @@ LpKernels lp_kernels() {
   };
   k.f32 = [](cudaStream_t st, int64_t n, const double* in, float* out) { k_lp_f32<<<kLpBlocks, 256, 0, st>>>(n, in, out); };
   k.scale = [](cudaStream_t st, int64_t n, float s, float* p) { k_lp_scale<<<kLpBlocks, 256, 0, st>>>(n, s, p); };
+  k.f32s = [](cudaStream_t st, int64_t n, double sc, const double* in, float* out) {
+    k_lp_f32s<<<kLpBlocks, 256, 0, st>>>(n, sc, in, out);
+  };
   return k;
 }
 

@@ -1,0 +1,473 @@
+// Warp-per-tet five-point operator kernel template (shared by the per-policy translation units).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "lp_ptx.cuh"
+#include "solver.h"
+
+namespace stdg {
+
+constexpr long kWarpSpin = 20000;   // x <= 1 ms suspend per try_wait
+
+struct WF32 { using TB = float; using XIn = float; using YOut = float; using Real = float; static constexpr int kPlanes = 1; };
+struct WBF16 { using TB = __nv_bfloat16; using XIn = float; using YOut = float; using Real = float; static constexpr int kPlanes = 1; };
+struct WDF { using TB = float; using XIn = double; using YOut = double; using Real = double; static constexpr int kPlanes = 2; };
+
+struct WarpArgs {
+  int ne, N, NR, NP, Nst, S, pinned, kron;
+  const int4* gface;            // per tet: (face << 1 | tet is r) or -1, 4 faces
+  const int4* gnbr;             // per tet: neighbour tet or -1
+  const void* Bd;               // diagonal blocks, padded layout
+  const void* Ao;               // face blocks A_lr, padded layout
+  uint32_t blk_bytes;           // one padded block (all planes)
+  uint32_t plane_elems;         // NR * NP
+  uint32_t xraw_off, stage_bytes, z_off, bar_off, warp_bytes;
+  double scale, pin_diag;
+  double Tacc[kMaxNg * kMaxNg];
+  // viscous operator (Eq. A1_mod): + mass_coef |J_i| (K (x) I) x_i, exact in the input precision
+  const double* detJ;
+  double mass_coef;
+  double Kmass[kMaxNg * kMaxNg];
+  int* err;
+};
+
+// four consecutive entries of a row (element index idx, a multiple of 4)
+__device__ __forceinline__ void load_row4(const float* B, int idx, float (&b)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(B + idx);
+  b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+}
+__device__ __forceinline__ void load_row4(const __nv_bfloat16* B, int idx, float (&b)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(B + idx);
+  b[0] = __uint_as_float(v.x << 16); b[1] = __uint_as_float(v.x & 0xFFFF0000u);
+  b[2] = __uint_as_float(v.y << 16); b[3] = __uint_as_float(v.y & 0xFFFF0000u);
+}
+__device__ __forceinline__ float load_one(const float* B, int idx) { return B[idx]; }
+__device__ __forceinline__ float load_one(const __nv_bfloat16* B, int idx) { return __bfloat162float(B[idx]); }
+
+// binary64-accurate multiply-add from binary32 pairs: (h, l) += (bh + bl)(zh + zl); the bl zl term
+// (relative size 2^-48) is left out
+__device__ __forceinline__ void df_fma(float& h, float& l, float bh, float bl, float zh, float zl) {
+  const float p = bh * zh;
+  float e = fmaf(bh, zh, -p);
+  e = fmaf(bh, zl, e);
+  e = fmaf(bl, zh, e);
+  float s, t;
+  df_two_sum(h, p, s, t);
+  h = s;
+  l += t + e;
+}
+
+__host__ __device__ constexpr int warp_np_c(int N) { return N % 8 == 4 ? N : warp_np_c(N + 1); }
+__host__ __device__ constexpr int warp_nr_c(int N) { return (N + 3) / 4 * 4; }
+
+// four entries of a block row (stride 1: one vector load) or column (stride NP: four loads) times
+// the matching z entries, accumulated into one chain per time column
+template <bool DF, int NG, typename TB>
+__device__ __forceinline__ void warp_chunk(const TB* B, int stride, uint32_t plane, const float* z, int NR,
+                                           int zplane, float (&h)[NG], float (&lo)[NG]) {
+  float bh[4], bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (stride == 1) {
+    load_row4(B, 0, bh);
+    if constexpr (DF) load_row4(B + plane, 0, bl);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bh[u] = load_one(B, u * stride);
+      if constexpr (DF) bl[u] = load_one(B + plane, u * stride);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    const float4 zh = *reinterpret_cast<const float4*>(z + q * NR);
+    if constexpr (DF) {
+      const float4 zl = *reinterpret_cast<const float4*>(z + zplane + q * NR);
+      df_fma(h[q], lo[q], bh[0], bl[0], zh.x, zl.x);
+      df_fma(h[q], lo[q], bh[1], bl[1], zh.y, zl.y);
+      df_fma(h[q], lo[q], bh[2], bl[2], zh.z, zl.z);
+      df_fma(h[q], lo[q], bh[3], bl[3], zh.w, zl.w);
+    } else {
+      h[q] = fmaf(bh[0], zh.x, h[q]);
+      h[q] = fmaf(bh[1], zh.y, h[q]);
+      h[q] = fmaf(bh[2], zh.z, h[q]);
+      h[q] = fmaf(bh[3], zh.w, h[q]);
+    }
+  }
+}
+
+template <typename W, int NG, int NC>
+__global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typename W::XIn* __restrict__ x,
+                                                    typename W::YOut* __restrict__ y) {
+  using TB = typename W::TB;
+  using XIn = typename W::XIn;
+  using Real = typename W::Real;
+  constexpr bool kDF = W::kPlanes == 2;
+  constexpr bool kDirectZ = !kDF && NC != 0 && NC % 4 == 0;
+  extern __shared__ __align__(128) unsigned char wsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  unsigned char* base = wsm + (size_t)warp * a.warp_bytes;
+  float* zs = reinterpret_cast<float*>(base + a.z_off);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + a.bar_off);
+  // NC != 0: N known at compile time (row loops fully unrolled, shared-memory offsets immediate)
+  const int N = NC ? NC : a.N, NR = NC ? warp_nr_c(NC) : a.NR, NP = NC ? warp_np_c(NC) : a.NP;
+  const int Nst = NC ? NC * NG : a.Nst, S = a.S;
+  const int zplane = 5 * NG * NR;
+  const int ZR = kDirectZ ? N : NR;                 // row stride of z
+  for (int e = lane; e < W::kPlanes * zplane; e += 32) zs[e] = 0.0f;     // padding entries stay 0
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 33);   // lane 0's expect_tx + 32 cp.async arrivals
+    fence_async_smem();
+  }
+  __syncwarp();
+
+  auto issue = [&](int i, int st, const int4& gf, const int4& gn) {
+    unsigned char* sb = base + (size_t)st * a.stage_bytes;
+    XIn* xr = reinterpret_cast<XIn*>(sb + a.xraw_off);
+    const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
+    const int nn[4] = {gn.x, gn.y, gn.z, gn.w};
+    if (lane == 0) {
+      uint32_t bytes = a.blk_bytes;
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fj[f] >= 0) bytes += a.blk_bytes;
+      fence_async_smem();                         // earlier generic reads of this stage before the copies
+      mbar_expect_tx(&bar[st], bytes);
+      tma_load_1d(sb, static_cast<const unsigned char*>(a.Bd) + (size_t)i * a.blk_bytes, a.blk_bytes, &bar[st]);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fj[f] >= 0)
+          tma_load_1d(sb + (size_t)(f + 1) * a.blk_bytes,
+                      static_cast<const unsigned char*>(a.Ao) + (size_t)(fj[f] >> 1) * a.blk_bytes, a.blk_bytes,
+                      &bar[st]);
+    }
+#pragma unroll
+    for (int sl = 0; sl < 5; ++sl) {
+      const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
+      if (nb < 0) continue;
+      const XIn* src = x + (size_t)nb * Nst;
+      for (int o = lane; o < Nst; o += 32) cp_async<sizeof(XIn)>(xr + sl * Nst + o, src + o);
+    }
+    cp_async_mbar_arrive_noinc(&bar[st]);
+  };
+
+  const int nw = gridDim.x * wpc;
+  int i = blockIdx.x * wpc + warp;
+  const int4 none = make_int4(-1, -1, -1, -1);
+  int4 gf_c = none, gn_c = none, gf_n = none, gn_n = none;
+  // iteration it uses stage it % S in its use number it / S (mbarrier phase parity (it / S) & 1)
+  bool abort = false, next_issued = false;
+  int it = 0;
+  if (i < a.ne) {
+    gf_c = a.gface[i]; gn_c = a.gnbr[i];
+    issue(i, 0, gf_c, gn_c);
+    if (S == 2 && i + nw < a.ne) { gf_n = a.gface[i + nw]; gn_n = a.gnbr[i + nw]; }
+  }
+  for (; i < a.ne; i += nw, ++it) {
+    const int st = S == 2 ? (it & 1) : 0;
+    const int inx = i + nw;
+    const int4 gf = gf_c, gn = gn_c;
+    next_issued = false;
+    if (S == 2 && inx < a.ne) {                   // next tet's copies run while this one computes
+      issue(inx, st ^ 1, gf_n, gn_n);
+      next_issued = true;
+      gf_c = gf_n; gn_c = gn_n;
+      if (inx + nw < a.ne) { gf_n = a.gface[inx + nw]; gn_n = a.gnbr[inx + nw]; }
+    }
+    {
+      long spins = 0;
+      const uint32_t par = (uint32_t)((it / S) & 1);
+      while (!mbar_wait_hint(&bar[st], par))
+        if (++spins > kWarpSpin) { abort = true; break; }
+    }
+    if (__any_sync(0xffffffffu, abort)) { abort = true; break; }
+    __syncwarp();
+    const unsigned char* sb = base + (size_t)st * a.stage_bytes;
+    const XIn* xr = reinterpret_cast<const XIn*>(sb + a.xraw_off);
+    const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
+    const int nn[4] = {gn.x, gn.y, gn.z, gn.w};
+    // x rows -> z planes (binary32, or the (hi, lo) split); pinned entries read as 0.  With
+    // binary32 x and rows already a multiple of 4 long, z is read in place from the staged rows.
+    if constexpr (kDirectZ) {
+      if (a.pinned) {
+#pragma unroll
+        for (int sl = 0; sl < 5; ++sl) {
+          const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
+          if (nb == 0 && lane < NG) const_cast<XIn*>(xr)[sl * Nst + lane * N] = (XIn)0;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int sl = 0; sl < 5; ++sl) {
+        const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
+        if (nb < 0) continue;
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+          for (int l = lane; l < N; l += 32) {
+            XIn v = xr[sl * Nst + q * N + l];
+            if (a.pinned && nb == 0 && l == 0) v = (XIn)0;
+            float* zq = zs + (sl * NG + q) * NR + l;
+            if constexpr (kDF) {
+              const float2 hl = df_split(v);
+              zq[0] = hl.x;
+              zq[zplane] = hl.y;
+            } else {
+              zq[0] = v;
+            }
+          }
+      }
+    }
+    __syncwarp();
+    const TB* blk = reinterpret_cast<const TB*>(sb);
+    const int blk_elems = (int)(a.blk_bytes / sizeof(TB));
+    int pres = 1, trm = 0;                        // per slot: block present / read transposed
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      pres |= (fj[f] >= 0 ? 1 : 0) << (f + 1);
+      trm |= (fj[f] >= 0 && (fj[f] & 1) ? 1 : 0) << (f + 1);
+    }
+    for (int k = lane; k < N; k += 32) {
+      float h0[NG], l0[NG], h1[NG], l1[NG];       // two accumulator chains per time column
+#pragma unroll
+      for (int q = 0; q < NG; ++q) { h0[q] = h1[q] = 0.0f; l0[q] = l1[q] = 0.0f; }
+      for (int sl = 0; sl < 5; ++sl) {
+        if (!((pres >> sl) & 1)) continue;
+        const TB* B = blk + sl * blk_elems;
+        const float* z = kDirectZ ? reinterpret_cast<const float*>(xr) + sl * Nst : zs + sl * NG * NR;
+        if (!((trm >> sl) & 1)) {                 // row k of the block, 4 entries per vector load
+          const TB* Br = B + k * NP;
+#pragma unroll
+          for (int l = 0; l < NR; l += 8) {
+            warp_chunk<kDF, NG>(Br + l, 1, a.plane_elems, z + l, ZR, zplane, h0, l0);
+            if (l + 4 < NR) warp_chunk<kDF, NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, ZR, zplane, h1, l1);
+          }
+        } else {                                  // column k: A_rl = A_lr^T, one word per lane
+          const TB* Bc = B + k;
+#pragma unroll
+          for (int l = 0; l < NR; l += 8) {
+            warp_chunk<kDF, NG>(Bc + l * NP, NP, a.plane_elems, z + l, ZR, zplane, h0, l0);
+            if (l + 4 < NR) warp_chunk<kDF, NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, ZR, zplane, h1, l1);
+          }
+        }
+      }
+      Real v[NG];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        if constexpr (kDF) {
+          float s, t;
+          df_two_sum(h0[q], h1[q], s, t);
+          v[q] = (double)s + ((double)t + (double)l0[q] + (double)l1[q]);
+        } else {
+          v[q] = h0[q] + h1[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        Real o = v[q];
+        if (!a.kron) {
+          o = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) o += (Real)a.Tacc[q * NG + b] * v[b];
+        }
+        o *= (Real)a.scale;
+        if (a.mass_coef != 0.0) {                 // x_i as staged (binary64 for the pair policy)
+          Real m = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) m += (Real)a.Kmass[q * NG + b] * (Real)xr[b * N + k];
+          o += (Real)(a.mass_coef * a.detJ[i]) * m;
+        }
+        if (a.pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
+        y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
+      }
+    }
+    __syncwarp();
+    if (S == 1 && inx < a.ne) {                   // one stage: the next tet's copies start now
+      gf_c = a.gface[inx]; gn_c = a.gnbr[inx];
+      issue(inx, 0, gf_c, gn_c);
+    }
+  }
+  if (abort) {
+    if (lane == 0) atomicExch(a.err, 1);
+    // bounded wait for this warp's copies in flight: the stage of iteration it and, when it was
+    // issued, the stage of iteration it + 1
+    const int st = S == 2 ? (it & 1) : 0;
+    long spins = 0;
+    while (!mbar_wait_hint(&bar[st], (uint32_t)((it / S) & 1)) && ++spins < kWarpSpin) {
+    }
+    if (next_issued) {
+      spins = 0;
+      while (!mbar_wait_hint(&bar[st ^ 1], (uint32_t)(((it + 1) / S) & 1)) && ++spins < kWarpSpin) {
+      }
+    }
+  }
+}
+
+// padded block copies: dst block b = planes x NR x NP, zero outside N x N
+template <typename TB, int PLANES>
+__global__ void k_to_padded(int64_t nblk, int N, int NR, int NP, const double* __restrict__ src, TB* __restrict__ dst,
+                            const double* __restrict__ src2 = nullptr, double c2 = 0.0) {
+  const int64_t per = (int64_t)PLANES * NR * NP;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nblk * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per;
+    const int rem = (int)(e - b * per);
+    const int plane = rem / (NR * NP);
+    const int rc = rem - plane * NR * NP;
+    const int r = rc / NP, c = rc - r * NP;
+    double v = (r < N && c < N) ? src[b * N * N + r * N + c] : 0.0;
+    if (src2 && r < N && c < N) v += c2 * src2[b * N * N + r * N + c];
+    if constexpr (sizeof(TB) == 2) {
+      dst[e] = __float2bfloat16_rn((float)v);
+    } else if constexpr (PLANES == 2) {
+      const float hi = (float)v;
+      dst[e] = plane == 0 ? hi : (float)(v - (double)hi);
+    } else {
+      dst[e] = (float)v;
+    }
+  }
+}
+
+static int warp_np(int N) { int np = N; while (np % 8 != 4) ++np; return np; }
+static int warp_nr(int N) { return (N + 3) / 4 * 4; }
+static uint32_t a16(size_t b) { return (uint32_t)((b + 15) & ~(size_t)15); }
+
+template <typename W>
+static cudaError_t ensure_warp_blocks(stdg_solver* s, void** Bd, void** Ao) {
+  if (*Bd) return cudaSuccess;
+  using TB = typename W::TB;
+  const int N = s->N, NR = warp_nr(N), NP = warp_np(N);
+  const size_t per = (size_t)W::kPlanes * NR * NP;
+  cudaError_t e = cudaMalloc(Bd, (size_t)s->ne * per * sizeof(TB));
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(*Bd);
+  e = cudaMalloc(Ao, (size_t)s->nf * per * sizeof(TB));
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(*Ao);
+  k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->ne, N, NR, NP, s->Bdiag, static_cast<TB*>(*Bd));
+  k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->nf, N, NR, NP, s->Aoff, static_cast<TB*>(*Ao));
+  s->nlaunch += 2;
+  return cudaGetLastError();
+}
+
+// padded copy of the viscous diagonal blocks B_i - Bvisc_i (Eq. A1_mod, with the face blocks A_lr)
+template <typename W>
+static cudaError_t ensure_warp_visc_diag(stdg_solver* s, void** Bv) {
+  if (*Bv || !s->Bvisc) return cudaSuccess;
+  using TB = typename W::TB;
+  const int N = s->N, NR = warp_nr(N), NP = warp_np(N);
+  cudaError_t e = cudaMalloc(Bv, (size_t)s->ne * W::kPlanes * NR * NP * sizeof(TB));
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(*Bv);
+  k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->ne, N, NR, NP, s->Bdiag, static_cast<TB*>(*Bv), s->Bvisc, -1.0);
+  ++s->nlaunch;
+  return cudaGetLastError();
+}
+
+static WarpArgs warp_layout(const stdg_solver* s, size_t tb, int planes, size_t xin, int S) {
+  WarpArgs a{};
+  a.ne = (int)s->ne; a.N = s->N; a.NR = warp_nr(s->N); a.NP = warp_np(s->N); a.Nst = s->Nst; a.S = S;
+  a.plane_elems = (uint32_t)(a.NR * a.NP);
+  a.blk_bytes = (uint32_t)(planes * a.plane_elems * tb);
+  a.xraw_off = 5 * a.blk_bytes;
+  a.stage_bytes = a.xraw_off + a16((size_t)5 * s->Nst * xin);
+  a.z_off = S * a.stage_bytes;
+  a.bar_off = a.z_off + a16((size_t)planes * 5 * s->Ng * a.NR * sizeof(float));
+  a.warp_bytes = a16(a.bar_off + 2 * sizeof(uint64_t));
+  return a;
+}
+
+template <typename W>
+static WarpArgs warp_args(const stdg_solver* s) {
+  // two stages when ten warps fit on an SM with them, else one (more warps hide the latency)
+  WarpArgs a = warp_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 2);
+  if ((size_t)a.warp_bytes * 10 > 228 * 1024) a = warp_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 1);
+  return a;
+}
+
+template <typename W>
+static constexpr int warp_kind() { return W::kPlanes == 2 ? 2 : (sizeof(typename W::TB) == 4 ? 1 : 0); }
+
+template <typename W>
+using WarpKernel = void (*)(WarpArgs, const typename W::XIn*, typename W::YOut*);
+
+// the instantiation for this N: compile-time N for p = 2, 3, 4, runtime N otherwise
+template <typename W, int NG>
+static WarpKernel<W> warp_kernel(int N) {
+  switch (N) {
+    case 10: return k_apply_warp<W, NG, 10>;
+    case 20: return k_apply_warp<W, NG, 20>;
+    case 35: return k_apply_warp<W, NG, 35>;
+    default: return k_apply_warp<W, NG, 0>;
+  }
+}
+
+// Launch shape (warps per CTA, persistent grid) from the occupancy of this layout; sets the
+// kernel's dynamic shared-memory limit.  Host-side setup: must not run during stream capture.
+template <typename W, int NG>
+static cudaError_t warp_configure(stdg_solver* s) {
+  const WarpArgs a = warp_args<W>(s);
+  const WarpKernel<W> kern = warp_kernel<W, NG>(s->N);
+  int& grid = s->warp_grid[warp_kind<W>() * 8 + NG];
+  int& wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
+  if (grid != 0) return cudaSuccess;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+  int best = 0, bw = 1;
+  for (int c : {4, 2, 1}) {
+    const size_t smem = (size_t)c * a.warp_bytes;
+    if (smem > 227 * 1024) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) continue;
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * c, smem);
+    if (per * c > best) { best = per * c; bw = c; }
+  }
+  cudaGetLastError();
+  if (best == 0) return cudaErrorInvalidConfiguration;      // the blocks of one tet do not fit on an SM
+  wpc = bw;
+  grid = nsm * (best / bw);
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)wpc * a.warp_bytes));
+}
+
+template <typename W>
+static cudaError_t warp_prepare_t(stdg_solver* s, void** Bd, void** Ao) {
+  cudaError_t e = ensure_warp_blocks<W>(s, Bd, Ao);
+  if (e != cudaSuccess) return e;
+  switch (s->Ng) {
+    case 1: return warp_configure<W, 1>(s);
+    case 2: return warp_configure<W, 2>(s);
+    case 3: return warp_configure<W, 3>(s);
+    case 4: return warp_configure<W, 4>(s);
+    default: return warp_configure<W, 5>(s);
+  }
+}
+
+template <typename W, int NG>
+static cudaError_t launch_warp_ng(stdg_solver* s, const WarpArgs& a, const typename W::XIn* x, typename W::YOut* y) {
+  const int grid = s->warp_grid[warp_kind<W>() * 8 + NG], wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
+  if (grid == 0) return cudaErrorNotReady;                  // warp_prepare has not run
+  warp_kernel<W, NG>(s->N)<<<grid, 32 * wpc, (size_t)wpc * a.warp_bytes, s->stream>>>(a, x, y);
+  return cudaGetLastError();
+}
+
+template <typename W>
+static cudaError_t launch_warp(stdg_solver* s, const void* Bd, const void* Ao, const typename W::XIn* x,
+                               typename W::YOut* y, int pinned, int kron, double scale, double pin_diag,
+                               double mass_coef = 0.0, const double* Kmass = nullptr) {
+  if (!Bd) return cudaErrorNotReady;
+  WarpArgs a = warp_args<W>(s);
+  a.gface = reinterpret_cast<const int4*>(s->gface);
+  a.gnbr = reinterpret_cast<const int4*>(s->gnbr);
+  a.Bd = Bd; a.Ao = Ao;
+  a.pinned = pinned; a.kron = kron; a.scale = scale; a.pin_diag = pin_diag;
+  for (int q = 0; q < s->Ng * s->Ng; ++q) a.Tacc[q] = s->tm.Tp[q];
+  a.detJ = s->dm.detJ;
+  a.mass_coef = Kmass ? mass_coef : 0.0;
+  for (int q = 0; Kmass && q < s->Ng * s->Ng; ++q) a.Kmass[q] = Kmass[q];
+  a.err = s->derr;
+  switch (s->Ng) {
+    case 1: return launch_warp_ng<W, 1>(s, a, x, y);
+    case 2: return launch_warp_ng<W, 2>(s, a, x, y);
+    case 3: return launch_warp_ng<W, 3>(s, a, x, y);
+    case 4: return launch_warp_ng<W, 4>(s, a, x, y);
+    default: return launch_warp_ng<W, 5>(s, a, x, y);
+  }
+}
+
+}  // namespace stdg

@@ -50,8 +50,10 @@ struct stdg_solver {
   int *gface = nullptr, *gnbr = nullptr;      // per-tet gather tables (int4 each) for the TMA kernels
   void *wB = nullptr, *wA = nullptr;          // warp-kernel block copies (binary32 / bfloat16), padded rows
   void *wdB = nullptr, *wdA = nullptr;        // warp-kernel (hi, lo) binary32 planes of the FP64 blocks
+  void *wdBv = nullptr;                       // same for the viscous diagonal blocks B_i - Bvisc_i
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
+  int mix_inner = 50;                         // binary32 CG iterations per outer step of the mixed solve
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
   float *fr = nullptr, *fp = nullptr, *fq = nullptr, *fz = nullptr, *fx = nullptr, *fb = nullptr;
   double* dmix = nullptr;                     // device copy of K (time mixing)
@@ -108,14 +110,18 @@ struct LpKernels {
   void (*accum)(cudaStream_t, int64_t, double, const float*, double*);
   void (*f32)(cudaStream_t, int64_t, const double*, float*);
   void (*scale)(cudaStream_t, int64_t, float, float*);
+  void (*f32s)(cudaStream_t, int64_t, double, const double*, float*);
 };
 LpKernels lp_kernels();
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag);
+cudaError_t warp_prepare(stdg_solver* s, int precision);   // block copies + launch shape, outside capture
 cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
                                  float pin_diag);
 cudaError_t launch_apply_warp_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                                  double pin_diag);
+cudaError_t launch_apply_warp_df_visc(stdg_solver* s, const double* x, double* y, double scale, double mass_coef,
+                                      const double* Kmass);
 cudaError_t launch_apply_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                             double pin_diag);
 cudaError_t df_build_blocks(stdg_solver* s);

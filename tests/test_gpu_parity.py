@@ -128,11 +128,13 @@ def test_cg_rejects_pt_positive():
 
 
 @pytest.mark.parametrize("p,pt,npic", [(1, 0, 2), (2, 1, 2)])
-def test_step_matches_oracle(p, pt, npic):
-    """One full Picard pressure-correction step (Sec. 2.6) on Beltrami data."""
+@pytest.mark.parametrize("precision", ["fp64", "df32", "mixed_f32"])
+def test_step_matches_oracle(p, pt, npic, precision):
+    """One full Picard pressure-correction step (Sec. 2.6) on Beltrami data; df32 runs the
+    pressure and viscous operators on the binary64-accurate pair kernel."""
     import paper_1601_07384_gb300 as g
     prm = BeltramiParams(nu=0.1)
-    gs, d = setup(2, p, pt, dt=0.01)
+    gs, d = setup(2, p, pt, dt=0.01, precision=precision)
     gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
     gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
     st = gs.step(prm.nu, npic, method="kron_cg", tol=1e-13)
@@ -205,17 +207,10 @@ def test_initial_projection_matches_oracle():
     assert rel(U, Uo) <= 1e-12
 
 
-def test_large_mesh_sampled_rows():
-    """The workload of the timed benchmark (24^3 hexes x 6 = 82,944 tets, p = 3, p_t = 1):
-    sampled rows of A x computed one by one by the oracle."""
-    import paper_1601_07384_gb300 as g
-    v, t = kuhn_mesh(24, seed=0)
-    gs = g.Solver(g.Mesh(v, t), g.Reference(3, 1), 0.005)
-    om = Mesh(v, t)
-    d = SpaceTimeDG(om, 3, 1, 0.005)
-    x = np.random.default_rng(11).standard_normal((om.ne, d.Nst))
-    y = gs.pressure_apply(torch.from_numpy(x.ravel()).cuda(), pinned=False).cpu().numpy().reshape(om.ne, d.Nst)
-    rows = np.random.default_rng(12).choice(om.ne, 12, replace=False)
+def _oracle_rows(om, d, x, rows):
+    """Rows of the unpinned A x computed one by one from the literal space-time blocks:
+    gradient, M_j^-1, divergence per interior dual cell of each sampled tet (Eq. CS_19)."""
+    out = []
     for i in rows:
         yi = np.zeros(d.Nst)
         for f in range(4):
@@ -228,7 +223,53 @@ def test_large_mesh_sampled_rows():
             for c in range(3):
                 gg = np.linalg.solve(fb["M"], fb["Q"][0][c] @ x[l] + fb["Q"][1][c] @ x[r])
                 yi += fb["D"][s][c] @ gg
-        assert rel(y[i], yi) <= 1e-12
+        out.append(yi)
+    return out
+
+
+def test_large_mesh_sampled_rows():
+    """The workload of the timed benchmark (24^3 hexes x 6 = 82,944 tets, p = 3, p_t = 1):
+    sampled rows of A x computed one by one by the oracle, for the FP64 operator, the
+    binary32-pair operator (both to 1e-12) and the binary32 operator (to 4e-6)."""
+    import paper_1601_07384_gb300 as g
+    v, t = kuhn_mesh(24, seed=0)
+    om = Mesh(v, t)
+    d = SpaceTimeDG(om, 3, 1, 0.005)
+    x = np.random.default_rng(11).standard_normal((om.ne, d.Nst))
+    rows = np.random.default_rng(12).choice(om.ne, 12, replace=False)
+    expect = _oracle_rows(om, d, x, rows)
+    xd = torch.from_numpy(x.ravel()).cuda()
+    for prec, tol in (("fp64", 1e-12), ("df32", 1e-12), ("mixed_f32", 4e-6)):
+        gs = g.Solver(g.Mesh(v, t), g.Reference(3, 1), 0.005, precision=prec)
+        if prec == "mixed_f32":
+            y = gs.pressure_apply_f32(xd.float(), pinned=False).double().cpu().numpy()
+        else:
+            y = gs.pressure_apply(xd, pinned=False).cpu().numpy()
+        y = y.reshape(om.ne, d.Nst)
+        for i, yi in zip(rows, expect):
+            assert rel(y[i], yi) <= tol, (prec, i)
+        del gs
+
+
+def test_largest_mesh_sampled_rows():
+    """The largest configuration (40^3 hexes x 6 = 384,000 tets, p = 4, p_t = 4: 67.2 M pressure
+    unknowns, ~84 GB of blocks on the device): sampled rows of the FP64 and binary32-pair
+    operators against the oracle, one row at a time."""
+    import paper_1601_07384_gb300 as g
+    v, t = kuhn_mesh(40, seed=0)
+    om = Mesh(v, t)
+    d = SpaceTimeDG(om, 4, 4, 0.01)
+    x = np.random.default_rng(21).standard_normal((om.ne, d.Nst))
+    rows = np.concatenate([[0, om.ne - 1], np.random.default_rng(22).choice(om.ne, 6, replace=False)])
+    expect = _oracle_rows(om, d, x, rows)
+    xd = torch.from_numpy(x.ravel()).cuda()
+    for prec in ("fp64", "df32"):
+        gs = g.Solver(g.Mesh(v, t), g.Reference(4, 4), 0.01, precision=prec)
+        y = gs.pressure_apply(xd, pinned=False).cpu().numpy().reshape(om.ne, d.Nst)
+        for i, yi in zip(rows, expect):
+            assert rel(y[i], yi) <= 1e-12, (prec, i)
+        del gs
+        torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2)])
@@ -261,15 +302,17 @@ def test_preconditioned_and_mixed_solves_match_direct(n, p, pt, prec):
     assert np.linalg.norm(x - xd) <= 1e-5 * np.linalg.norm(xd)
 
 
-def test_bf16_refinement_stops_loudly_when_it_cannot_converge():
-    """With bfloat16 blocks the refinement contracts only if cond(A) * 2^-9 < 1, which these
-    pressure systems violate: the solve must stop with ENOCONV, not iterate to the cap."""
+def test_bf16_inner_solve_still_reaches_fp64_tolerance():
+    """bfloat16 blocks make a poor inner preconditioner (cond(A) * 2^-9 >> 1), but the binary64
+    outer flexible CG owns the residual: the solve reaches 1e-11 and agrees with the direct solve."""
     import paper_1601_07384_gb300 as g
     gs, d = setup(2, 2, 1, precision="mixed_bf16", max_iters=50000)
     b = np.random.default_rng(9).standard_normal((d.mesh.ne, d.Nst))
     b[0, ops.pin_index(d)] = 0.0
-    with pytest.raises(g.StdgError, match="ENOCONV"):
-        gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=1e-11, method="kron_pcg")
+    x, st = gs.solve(torch.from_numpy(b.ravel()).cuda(), tol=1e-11, method="kron_pcg")
+    A = ops.pressure_sparse(d)
+    assert np.linalg.norm(b.ravel() - A @ x.cpu().numpy()) <= 2e-11 * np.linalg.norm(b)
+    assert st["rel_residual"] <= 1e-11
 
 
 @pytest.mark.parametrize("n,p,pt", CASES)
