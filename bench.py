@@ -31,7 +31,8 @@ WORKLOADS = {
     "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
     "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50),
     "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
-    "learned": dict(n=12, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
+    "learned": dict(n=6, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
+    "theta": dict(n=24, p=3, pt=0, nu=0.01, dt=0.005, npic=2, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 # binary64-accurate products from binary32 pairs: 12 FP32 lane operations per multiply-add term
@@ -262,8 +263,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
     ap.add_argument("--solver", default="kron_pcg", choices=["kron_cg", "kron_pcg", "gmres"])
+    ap.add_argument("--theta", type=float, default=1.0,
+                    help="semi-implicit pressure weight (p_t = 0 workloads only; 1 = fully implicit)")
     ap.add_argument("--learned", action="store_true",
                     help="learned-preconditioner protocol: harvest + train on early steps, evaluate FGMRES later")
+    ap.add_argument("--graph-batch", type=int, default=8,
+                    help="Krylov iterations per captured CUDA graph (1: no graphs, e.g. for kernel-level profiling)")
     ap.add_argument("--op-only", type=int, default=0,
                     help="only build the workload and apply the pressure operator this many times (profiling)")
     args = ap.parse_args()
@@ -292,7 +297,8 @@ def main():
     v, t = kuhn_mesh(w["n"], seed=0)
     mesh = g.Mesh(v, t)
     ref = g.Reference(w["p"], w["pt"])
-    solver = g.Solver(mesh, ref, w["dt"], precision=args.precision, restart=w["restart"], max_iters=200000)
+    solver = g.Solver(mesh, ref, w["dt"], precision=args.precision, restart=w["restart"], max_iters=200000,
+                      graph_batch=args.graph_batch)
     fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
     if args.op_only > 0:
         ms = operator_alone_ms(solver, args.precision, args.op_only)
@@ -301,6 +307,8 @@ def main():
         return
     solver.set_initial(fld)
     solver.set_boundary(fld)
+    if args.theta != 1.0:
+        solver.set_theta(args.theta)
     stream = solver.stream
     for _ in range(args.warmup):
         solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
@@ -349,26 +357,29 @@ def main():
     barrier()
     e2e = (time.perf_counter() - te0) / args.steps
 
-    # ---- plain FP64 GMRES(50) on the same step (the paper's solver), from the same state
+    # ---- the paper's plain FP64 solver on the same step (GMRES(50); CG when p_t = 0), same state
     gm = None
     if args.gmres_steps > 0:
         solver.set_state(P0, V0, t0)
         gsolver = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=args.gmres_max_iters)
         gsolver.set_boundary(fld)
         gsolver.set_state(P0, V0, t0)
+        if args.theta != 1.0:
+            gsolver.set_theta(args.theta)
+        plain = "cg" if w["pt"] == 0 else "gmres"      # the paper's solver: CG when p_t = 0
         gts = []
         ok = True
         for _ in range(args.gmres_steps):
             torch.cuda.synchronize()
             tg0 = time.perf_counter()
             try:
-                st = gsolver.step(w["nu"], w["npic"], method="gmres", tol=w["tol"])
+                st = gsolver.step(w["nu"], w["npic"], method=plain, tol=w["tol"])
             except g.StdgError as exc:
                 ok = False
                 st = {"error": str(exc)}
             torch.cuda.synchronize()
             gts.append(time.perf_counter() - tg0)
-        gm = {"s_per_step": float(np.median(gts)) if ok else None, "converged": ok,
+        gm = {"method": plain, "s_per_step": float(np.median(gts)) if ok else None, "converged": ok,
               "max_iters_per_solve": args.gmres_max_iters,
               "press_iters": st.get("press_iters") if ok else None}
         if not ok:      # the first pressure solve hit the cap: a lower bound on the plain solver's step
@@ -421,7 +432,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "df32": "f64 (products from fp32 pairs)",
                                        "mixed_f32": "f64 outer (pair products) / f32 inner", "mixed_bf16": "f64 outer (pair products) / bf16 inner"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload_name(w), "solver": args.solver, "precision": args.precision,
+        "config": {"workload": workload_name(w) + (f", theta={args.theta}" if args.theta != 1.0 else ""),
+                   "solver": args.solver, "precision": args.precision,
                    "parallelism": f"replicas only: {world} independent copies" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
         "roofline": roof,
@@ -434,7 +446,10 @@ def main():
         "max_divergence": max(s["max_divergence"] for s in stats),
         "matvecs_per_s": ops_per_step / (ms / 1e3 / args.steps),
         "pressure_dof_updates_per_s": ops_per_step / (ms / 1e3 / args.steps) * solver.ne * solver.Nst,
-        "time_breakdown": {"operator_s_per_step": prof["operator_ms"] / 1e3 / args.steps,
+        "time_breakdown": {"phases_s_per_step": dict(zip(["slab setup", "averaging + Lambda", "convection", "viscous solves",
+                                                            "goback + pressure rhs", "pressure solve", "updates"],
+                                                           [v / 1e3 / args.steps for v in prof["phase_ms"][:7]])),
+                           "operator_s_per_step": prof["operator_ms"] / 1e3 / args.steps,
                            "rest_s_per_step": ms / 1e3 / args.steps - prof["operator_ms"] / 1e3 / args.steps,
                            "operator_kinds": {kinds[k]: {"launches_per_step": prof["kind_launches"][k] / args.steps,
                                                          "ms_per_launch": prof["kind_ms"][k] / max(prof["kind_launches"][k], 1)}

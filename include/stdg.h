@@ -307,6 +307,10 @@ typedef struct {
   double operator_ms;        /* summed CUDA-event time of the operator launches (enabled)  */
   int64_t kind_launches[4];  /* timed operator launches by kernel: [0] binary64 blocks,     */
   double kind_ms[4];         /* [1] binary32-pair blocks, [2] binary32, [3] bfloat16 blocks */
+  double phase_ms[8];        /* stdg_step by phase (CUDA events, enabled): [0] slab setup
+                                (averages, boundary data, trace), [1] averaging and Lambda,
+                                [2] convection, [3] viscous solves, [4] goback and pressure
+                                right-hand side, [5] pressure solve, [6] updates, [7] unused */
 } stdg_profile_stats;
 /* Reset the counters; enable != 0 also records a CUDA event pair around every operator
  * launch on the solver's stream (adds two event records per launch). */

@@ -291,7 +291,8 @@ class Solver:
         st = _lib.ProfileStats()
         _lib.check(_lib.load().stdg_profile_read(self._h, C.byref(st)))
         return {"kernel_launches": st.kernel_launches, "operator_launches": st.operator_launches,
-                "operator_ms": st.operator_ms, "kind_launches": list(st.kind_launches), "kind_ms": list(st.kind_ms)}
+                "operator_ms": st.operator_ms, "kind_launches": list(st.kind_launches), "kind_ms": list(st.kind_ms),
+                "phase_ms": list(st.phase_ms)}
 
     def blocks(self):
         N, nf, ne = self.N, self.nf, self.ne

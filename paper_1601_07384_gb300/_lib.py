@@ -35,7 +35,7 @@ class SolverOptions(C.Structure):
 
 class ProfileStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("operator_launches", C.c_int64), ("operator_ms", C.c_double),
-                ("kind_launches", C.c_int64 * 4), ("kind_ms", C.c_double * 4)]
+                ("kind_launches", C.c_int64 * 4), ("kind_ms", C.c_double * 4), ("phase_ms", C.c_double * 8)]
 
 
 class Field(C.Structure):

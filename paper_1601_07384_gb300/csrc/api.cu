@@ -79,6 +79,8 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
     s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
     const char* mi = std::getenv("STDG_MIXED_INNER");   // binary32 iterations per outer mixed step
     if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = std::atoi(mi);
+    const char* mm = std::getenv("STDG_MIXED_M");       // directions kept by the outer flexible CG
+    if (mm && std::atoi(mm) > 0 && std::atoi(mm) <= 16) s->mix_m = std::atoi(mm);
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;
@@ -365,6 +367,7 @@ extern "C" stdg_status stdg_profile(stdg_solver* s, int enable) {
   s->op_launches = 0;
   s->nlaunch = 0;
   for (int q = 0; q < 4; ++q) { s->kind_ms[q] = 0.0; s->kind_n[q] = 0; }
+  for (double& v : s->phase_ms) v = 0.0;
   return STDG_OK;
 }
 
@@ -378,5 +381,6 @@ extern "C" stdg_status stdg_profile_read(stdg_solver* s, stdg_profile_stats* out
   out->operator_launches = s->op_launches;
   out->operator_ms = s->op_ms;
   for (int q = 0; q < 4; ++q) { out->kind_launches[q] = s->kind_n[q]; out->kind_ms[q] = s->kind_ms[q]; }
+  for (int q = 0; q < 8; ++q) out->phase_ms[q] = s->phase_ms[q];
   return STDG_OK;
 }

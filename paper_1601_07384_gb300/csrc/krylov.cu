@@ -2,6 +2,7 @@
 // p_t = 0).  Every reduction is two-stage over a fixed grid, so results are bitwise
 // reproducible run to run.  Vectors use the pressure layout P[ne][Ng][N].
 #include <string>
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -49,10 +50,12 @@ __global__ void __launch_bounds__(kRedThreads) k_coldot(int64_t n, int N, int Ng
 
 // x += alpha_a p; r -= alpha_a q; partials of r.r per column (slot a) and of ||(I (x) Tp) r||^2 (slot Ng)
 struct TpArg { double v[kMaxNg * kMaxNg]; };
+// want = 0 (block-Jacobi PCG between convergence checks): only the x and r updates; the binary64
+// pipe is 1/64 of the binary32 rate on sm_103a, so the norms are not formed when nobody reads them.
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t ne, int N, int Ng, const double* __restrict__ alpha,
                                                           double* __restrict__ x, double* __restrict__ r,
                                                           const double* __restrict__ p, const double* __restrict__ q,
-                                                          TpArg Tp, double* part) {
+                                                          TpArg Tp, double* part, int want = 1) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double al[kMaxNg];
   for (int a = 0; a < Ng; ++a) al[a] = alpha[a];
@@ -68,15 +71,16 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t ne, int N, in
       double rn = fma(-al[a], q[o], r[o]);
       r[o] = rn;
       rv[a] = rn;
-      acc[a] = fma(rn, rn, acc[a]);
+      if (want) acc[a] = fma(rn, rn, acc[a]);
     }
-    for (int a = 0; a < Ng; ++a) {
-      double w = 0.0;
-      for (int b = 0; b < Ng; ++b) w = fma(Tp.v[a * Ng + b], rv[b], w);
-      acc[Ng] = fma(w, w, acc[Ng]);
-    }
+    if (want)
+      for (int a = 0; a < Ng; ++a) {
+        double w = 0.0;
+        for (int b = 0; b < Ng; ++b) w = fma(Tp.v[a * Ng + b], rv[b], w);
+        acc[Ng] = fma(w, w, acc[Ng]);
+      }
   }
-  block_reduce_store(acc, Ng + 1, part, Ng + 1);
+  if (want) block_reduce_store(acc, Ng + 1, part, Ng + 1);
 }
 
 // z_i[a][k] = Sum_l Binv_i[k][l] r_i[a][l]  (block Jacobi); partials of r.z per column a.
@@ -178,7 +182,12 @@ __global__ void k_cg_dir(int64_t n, int N, int Ng, const double* __restrict__ be
 }
 
 // out[c] = Sum_b part[b * width + c] in fixed order (one block per column)
-__global__ void k_final(int nparts, int width, const double* __restrict__ part, double* __restrict__ out) {
+__global__ void k_final(int nparts, int width, const double* __restrict__ part, double* __restrict__ out,
+                        const double* gate = nullptr) {
+  if (gate && gate[0] == 0.0) {                   // gated off: the result is 0
+    if (threadIdx.x == 0) out[blockIdx.x] = 0.0;
+    return;
+  }
   __shared__ double red[kRedThreads / 32];
   const int c = blockIdx.x;
   double s = 0.0;
@@ -223,10 +232,121 @@ __global__ void k_cg_beta_guard(int Ng, double* rz, const double* rznew, double*
   }
   if (a == 0) res[0] = flag[0] != 0.0 ? -1.0 : sqrt(mix2[0]);
 }
-// flexible CG: beta_a = -(z.Sp_prev)_a / (p_prev.Sp_prev)_a
-__global__ void k_fcg_beta(int Ng, const double* zq, const double* pqp, double* beta) {
-  const int a = threadIdx.x;
-  if (a < Ng) beta[a] = pqp[a] != 0.0 ? -zq[a] / pqp[a] : 0.0;
+// Preconditioner of the viscous systems (Eq. A1_mod): the inverse of their mass part,
+// z_i = (mass |J_i| K)^-1 (x) I r_i (K^-1 passed in Kinv), with partials of r.z per column.
+__global__ void __launch_bounds__(kRedThreads) k_visc_mass_inv(int64_t ne, int N, int Ng, TpArg Kinv, double mass,
+                                                              const double* __restrict__ detJ,
+                                                              const double* __restrict__ r, double* __restrict__ z,
+                                                              double* part) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int k = (int)(e % N);
+    const double c = 1.0 / (mass * detJ[i]);
+    double rv[kMaxNg];
+    for (int b = 0; b < Ng; ++b) rv[b] = r[i * Nst + b * N + k];
+    for (int a = 0; a < Ng; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < Ng; ++b) s = fma(Kinv.v[a * Ng + b], rv[b], s);
+      s *= c;
+      z[i * Nst + a * N + k] = s;
+      if (part) acc[a] = fma(s, rv[a], acc[a]);
+    }
+  }
+  if (part) block_reduce_store(acc, Ng, part, Ng);
+}
+
+// Classical Gram-Schmidt reorthogonalisation test ("twice is enough", Giraud et al. 2005): a second
+// pass is needed only when the first removed more than half of ||w||^2, i.e. when
+// ||w||^2 - Sum h^2 < ||w||^2 / 2 (cancellation then makes the left side small, so the test errs
+// towards reorthogonalising).  gate[0] = 1 if the second pass runs.
+__global__ void k_reorth_gate(int cnt, const double* h, const double* w2, double* gate) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < cnt; ++i) s = fma(h[i], h[i], s);
+  gate[0] = (w2[0] - s < 0.5 * w2[0]) ? 1.0 : 0.0;
+}
+
+// alpha_a = rz_a / (Sum of the partials of p.q)_a, one block per column (fixed order: deterministic)
+__global__ void k_final_alpha(int nparts, int Ng, const double* __restrict__ part, const double* rz, double* alpha) {
+  const int a = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * Ng + a];
+  __shared__ double red[kRedThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += red[q];
+    alpha[a] = t != 0.0 ? rz[a] / t : 0.0;
+  }
+}
+// rznew_a = Sum of the partials of r.z; beta_a = rznew_a / rz_a; rz_a = rznew_a
+__global__ void k_final_beta(int nparts, int Ng, const double* __restrict__ part, double* rz, double* beta) {
+  const int a = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * Ng + a];
+  __shared__ double red[kRedThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += red[q];
+    beta[a] = rz[a] != 0.0 ? t / rz[a] : 0.0;
+    rz[a] = t;
+  }
+}
+// res = sqrt of the reduced ||(I (x) Tp) r||^2 partials (slot Ng of width Ng + 1)
+__global__ void k_final_res(int nparts, int width, int slot, const double* __restrict__ part, double* res) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * width + slot];
+  __shared__ double red[kRedThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += red[q];
+    res[0] = sqrt(t);
+  }
+}
+// flexible CG with m stored directions: per direction j (blockIdx.y) and column a, partials of z.Q_j
+__global__ void __launch_bounds__(kRedThreads) k_fcg_dots(int64_t n, int N, int Ng, int m, const double* __restrict__ Qb,
+                                                         const double* __restrict__ z, double* part) {
+  const int j = blockIdx.y;
+  const double* Q = Qb + (size_t)j * n;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    acc[(e / N) % Ng] = fma(z[e], Q[e], acc[(e / N) % Ng]);
+  __shared__ double red[8][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < Ng; ++c) {
+    double s = warp_sum(acc[c]);
+    if (lane == 0) red[c][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < Ng) {
+    double s = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) s += red[threadIdx.x][q];
+    part[(size_t)blockIdx.x * m * Ng + j * Ng + threadIdx.x] = s;
+  }
+}
+// c[j][a] = -(z.Q_j)_a / (P_j.Q_j)_a
+__global__ void k_fcg_coef(int cnt, const double* zq, const double* pq, double* c) {
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) c[t] = pq[t] != 0.0 ? -zq[t] / pq[t] : 0.0;
+}
+// p = z + Sum_j c[j][a] P_j  (column a of each entry)
+__global__ void k_fcg_dir(int64_t n, int N, int Ng, int m, const double* __restrict__ c, const double* __restrict__ Pb,
+                          const double* __restrict__ z, double* __restrict__ p) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)((e / N) % Ng);
+    double v = z[e];
+    for (int j = 0; j < m; ++j) v = fma(c[j * Ng + a], Pb[(size_t)j * n + e], v);
+    p[e] = v;
+  }
 }
 // beta_a = rrnew_a / rr_a; rr <- rrnew; res = sqrt(tp2)
 __global__ void k_cg_beta(int Ng, double* rr, const double* rrnew, double* beta, double* res) {
@@ -258,7 +378,9 @@ __global__ void k_timemix(int64_t ne, int N, int Ng, TpArg M, double coef, const
 // GMRES helpers -------------------------------------------------------------------------------
 // part[v][b]: dot of basis vector v with w over this block's range
 __global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const double* __restrict__ Vb,
-                                                         const double* __restrict__ w, double* part) {
+                                                         const double* __restrict__ w, double* part,
+                                                         const double* gate = nullptr) {
+  if (gate && gate[0] == 0.0) return;             // second Gram-Schmidt pass not needed
   const int v = blockIdx.y;
   const double* vv = Vb + (size_t)v * n;
   double acc = 0.0;
@@ -276,7 +398,8 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const doubl
 }
 // w += sign Sum_v h[v] V[v]
 __global__ void k_multiaxpy(int64_t n, int nv, const double* __restrict__ Vb, const double* __restrict__ h,
-                            double sign, double* __restrict__ w) {
+                            double sign, double* __restrict__ w, const double* gate = nullptr) {
+  if (gate && gate[0] == 0.0) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int v = 0; v < nv; ++v) s = fma(h[v], Vb[(size_t)v * n + e], s);
@@ -399,13 +522,95 @@ stdg_status apply_pressure(stdg_solver* s, const double* x, double* y, int pinne
   return op_apply(s, pressure_op(s, pinned, kron, scale, pin_diag), x, y);
 }
 
+// A batch of B iterations of `body` captured once into a CUDA graph and replayed on the solver's
+// internal stream, ordered after and before the caller's stream by events (the caller's stream may
+// be a legacy stream that cannot be captured).
+struct GraphLoop {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int B = 0;
+  bool prof = false;
+  ~GraphLoop() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+static stdg_status graph_streams(stdg_solver* s, int B) {
+  if (!s->cstream) {
+    if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->sync_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->sync_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("internal stream creation failed");
+      return STDG_ECUDA;
+    }
+  }
+  if ((int)s->gev.size() < 2 * B) {
+    for (cudaEvent_t e : s->gev) cudaEventDestroy(e);
+    s->gev.assign(2 * B, nullptr);
+    for (auto& e : s->gev)
+      if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return STDG_ECUDA; }
+  }
+  return STDG_OK;
+}
+
+template <typename Body>
+static stdg_status graph_capture(stdg_solver* s, int B, Body body, GraphLoop& g) {
+  stdg_status st = graph_streams(s, B);
+  if (st != STDG_OK) return st;
+  cudaStream_t user = s->stream;
+  s->stream = s->cstream;
+  g.prof = s->prof;
+  g.B = B;
+  s->capturing = true;
+  if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    s->capturing = false; s->stream = user;
+    set_error("stream capture failed to start");
+    return STDG_ECUDA;
+  }
+  for (int j = 0; j < B && st == STDG_OK; ++j) st = body(j, g.prof ? &s->gev[2 * j] : nullptr);
+  cudaError_t ce = cudaStreamEndCapture(s->stream, &g.graph);
+  s->capturing = false;
+  s->stream = user;
+  if (st != STDG_OK) return st;
+  if (ce != cudaSuccess || cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+    set_error("graph capture/instantiation failed: %s", cudaGetErrorString(ce));
+    return STDG_ECUDA;
+  }
+  return STDG_OK;
+}
+
+static stdg_status graph_launch(stdg_solver* s, GraphLoop& g, int kernels_per_iter, int kind) {
+  cudaEventRecord(s->sync_ev[0], s->stream);
+  cudaStreamWaitEvent(s->cstream, s->sync_ev[0], 0);
+  if (cudaGraphLaunch(g.exec, s->cstream) != cudaSuccess) {
+    set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return STDG_ECUDA;
+  }
+  cudaEventRecord(s->sync_ev[1], s->cstream);
+  cudaStreamWaitEvent(s->stream, s->sync_ev[1], 0);
+  s->nlaunch += (int64_t)g.B * kernels_per_iter;
+  s->op_launches += g.B;
+  if (g.prof) {
+    if (cudaStreamSynchronize(s->cstream) != cudaSuccess) { set_error("graph launch failed"); return STDG_ECUDA; }
+    for (int j = 0; j < g.B; ++j) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, s->gev[2 * j], s->gev[2 * j + 1]);
+      s->op_ms += ms;
+      s->kind_ms[kind] += ms;
+      s->kind_n[kind] += 1;
+    }
+  }
+  return STDG_OK;
+}
+
 // Run `body` (one Krylov iteration that ends by copying its residual to host_slot) in batches of
 // B iterations captured once into a CUDA graph and replayed on an internal stream; the caller's
 // stream is ordered before and after by events.  Up to B-1 iterations may run past convergence;
 // they are counted.  Operator launches inside the graph are timed by dedicated event nodes.
 template <typename Body>
 static stdg_status run_batched(stdg_solver* s, int B, int kernels_per_iter, int max_it, double tol_abs, Body body,
-                               int* iters, double* rabs_out, int kind) {
+                               int* iters, double* rabs_out, int kind, bool last_only = false) {
   if (!s->cstream) {
     if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->sync_ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -462,7 +667,7 @@ static stdg_status run_batched(stdg_solver* s, int B, int kernels_per_iter, int 
       }
     }
     bool done = false;
-    for (int j = 0; j < B; ++j) {
+    for (int j = last_only ? B - 1 : 0; j < B; ++j) {
       rabs = s->hostbuf[j];
       if (!std::isfinite(rabs)) { set_error("Krylov: non-finite residual"); st = STDG_ENAN; break; }
       if (rabs <= tol_abs) { done = true; }
@@ -530,37 +735,43 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   }
   ++s->nlaunch;
   k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
-  // one CG iteration; ends by copying the full-system residual norm to the host
+  // one CG iteration; ends by copying the full-system residual norm to the host.  With the
+  // preconditioner, inside a captured batch only the batch's last iteration forms the norm (the
+  // host reads only that one), and the step length / beta come from fused reduction kernels.
+  const int Bb = s->opt.graph_batch > 1 ? s->opt.graph_batch : 1;
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
-    // inside a captured graph an event-record node only joins the dependency chain if later work
-    // waits on it, so each record is followed by a wait on the same event
     if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
     stdg_status e = op_apply(s, op, p, q);
     if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
     if (e != STDG_OK) return e;
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
+    if (precond) {
+      const int want = slot == Bb - 1;
+      k_final_alpha<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, alpha);
+      k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part, want);
+      if (want) k_final_res<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, Ng, s->part, res);
+      k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
+      k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, beta);
+      k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, z, p);
+      if (want) cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+      return STDG_OK;
+    }
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
     k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha);
     k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part);
     k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
-    if (precond) {
-      k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
-      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
-      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng);
-    } else {
-      k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rrnew, beta, res, rrnew + Ng);
-    }
-    k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, precond ? z : r, p);
+    k_cg_beta2<<<1, 32, 0, s->stream>>>(Ng, rz, rrnew, beta, res, rrnew + Ng);
+    k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, r, p);
     cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     return STDG_OK;
   };
-  const int kpi = precond ? 9 : 7;
+  const int kpi = precond ? 7 : 8;
   int it = 0;
   double rabs = INFINITY;
   const int maxit = s->opt.max_iters;
   if (s->opt.graph_batch > 1) {
     const int kind = df_serves(s, op) ? 1 : 0;
-    stdg_status e = run_batched(s, s->opt.graph_batch, kpi, maxit, tol_abs, body, &it, &rabs, kind);
+    stdg_status e = run_batched(s, s->opt.graph_batch, kpi, maxit, tol_abs, body, &it, &rabs, kind, precond);
     if (e != STDG_OK) return e;
   } else {
     while (it < maxit) {
@@ -585,8 +796,8 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
 // Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations on the host.
 // x holds the initial guess unless zero_x0.  Stops when ||b - A x|| <= tol_abs.
 static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
-                         double tol_abs, int* iters, int* nrestarts, double* res_abs) {
-  const int m = s->opt.restart;
+                         double tol_abs, int* iters, int* nrestarts, double* res_abs, int restart = 0) {
+  const int m = restart > 0 ? restart : s->opt.restart;
   const int64_t n = s->ne * (int64_t)s->Nst;
   stdg_status e = ensure_basis(s, m + 1);
   if (e != STDG_OK) return e;
@@ -615,15 +826,18 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
       double* w = s->basis + (size_t)(k + 1) * n;
       e = op_apply(s, op, s->basis + (size_t)k * n, w);
       if (e != STDG_OK) return e;
+      // classical Gram-Schmidt, second pass only when the first cancelled (gate at hd[260])
+      k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
+      k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, s->part, hd + 258);
       for (int pass = 0; pass < 2; ++pass) {
         double* hp = hd + pass * 128;
-        ++s->nlaunch;
-        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part);
-        ++s->nlaunch;
-        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp);
-        ++s->nlaunch;
-        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w);
+        const double* gate = pass == 0 ? nullptr : hd + 260;
+        if (pass == 1) k_reorth_gate<<<1, 32, 0, s->stream>>>(k + 1, hd, hd + 258, hd + 260);
+        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part, gate);
+        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp, gate);
+        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w, gate);
       }
+      s->nlaunch += 9;
       ++s->nlaunch;
       k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
       ++s->nlaunch;
@@ -675,7 +889,9 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
 // cycle's search space then contains the block-Jacobi cycle's, so its residual is never larger
 // than that cycle's would be from the same start, whatever the network returns.
 static stdg_status fgmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
-                          double tol_abs, int* iters, int* nrestarts, double* res_abs, int use_gnn) {
+                          double tol_abs, int* iters, int* nrestarts, double* res_abs, int use_gnn, bool visc = false) {
+  TpArg Kinv{};
+  for (int c = 0; c < s->Ng * s->Ng; ++c) Kinv.v[c] = s->Kinv[c];
   const int m0 = s->opt.restart;
   const int m = m0 + (use_gnn ? 1 : 0);            // directions per cycle
   const int64_t n = s->ne * (int64_t)s->Nst;
@@ -706,19 +922,29 @@ static stdg_status fgmres(stdg_solver* s, const ApplyArgs& op, const double* b, 
     for (k = 0; k < m; ++k) {
       double* w = s->basis + (size_t)(k + 1) * n;
       double* zk = s->kzz + (size_t)k * n;
-      e = k < m0 ? gnn_precond(s, s->basis + (size_t)k * n, zk, 0) : gnn_precond(s, s->basis, zk, 1);
+      if (visc) {                                 // viscous systems: inverse of the mass part
+        k_visc_mass_inv<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, s->N, s->Ng, Kinv, op.mass_coef, op.detJ,
+                                                                    s->basis + (size_t)k * n, zk, nullptr);
+        ++s->nlaunch;
+        e = STDG_OK;
+      } else {
+        e = k < m0 ? gnn_precond(s, s->basis + (size_t)k * n, zk, 0) : gnn_precond(s, s->basis, zk, 1);
+      }
       if (e != STDG_OK) return e;
       e = op_apply(s, op, zk, w);
       if (e != STDG_OK) return e;
+      // classical Gram-Schmidt, second pass only when the first cancelled (gate at hd[260])
+      k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
+      k_final<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, 1, s->part, hd + 258);
       for (int pass = 0; pass < 2; ++pass) {
         double* hp = hd + pass * 128;
-        ++s->nlaunch;
-        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part);
-        ++s->nlaunch;
-        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp);
-        ++s->nlaunch;
-        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w);
+        const double* gate = pass == 0 ? nullptr : hd + 260;
+        if (pass == 1) k_reorth_gate<<<1, 32, 0, s->stream>>>(k + 1, hd, hd + 258, hd + 260);
+        k_multidot<<<dim3(kRedBlocks, k + 1), kRedThreads, 0, s->stream>>>(n, s->basis, w, s->part, gate);
+        k_final<<<k + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, k + 1, s->part, hp, gate);
+        k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k + 1, s->basis, hp, -1.0, w, gate);
       }
+      s->nlaunch += 9;
       ++s->nlaunch;
       k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
       ++s->nlaunch;
@@ -784,18 +1010,20 @@ static stdg_status ensure_lowprec(stdg_solver* s) {
 
 // Mixed precision, inner-outer.  Outer: flexible CG in binary64 on the Kronecker-decoupled system
 // S X = B' (S = -A_sp (x) I with the pin, B' = -(I (x) Tp^-1) b), operator applied by the
-// binary64-accurate pair kernel; each direction is S-orthogonalised against the previous one
-// (flexible CG with one stored direction, Notay 2000), and x, r and all scalars are binary64, so the
-// binary32 parts change how fast it converges, not the accuracy it reaches.  Preconditioner:
-// s->mix_inner iterations of block-Jacobi CG in binary32 (binary32 or bfloat16 operator, binary32
-// vectors) started from zero on S d = r / ||r||.  Stops when ||(I (x) Tp) r|| (the full-system
-// residual) <= tol ||b||.
+// binary64-accurate pair kernel; each new direction is S-orthogonalised against the last m
+// directions (flexible CG, Notay 2000), and x, r and all scalars are binary64, so the binary32 parts
+// change how fast it converges, not the accuracy it reaches.  Preconditioner: s->mix_inner
+// iterations of block-Jacobi CG in binary32 (binary32 or bfloat16 operator, binary32 vectors)
+// started from zero on S d = r / ||r||, captured once per solve as a CUDA graph.  Stops when
+// ||(I (x) Tp) r|| (the full-system residual) <= tol ||b||.
 static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, double tol, double bn, int* iters,
                                int* outer, double* res_abs) {
   stdg_status e = ensure_lowprec(s);
   if (e != STDG_OK) return e;
-  const int N = s->N, Ng = s->Ng;
+  const int N = s->N, Ng = s->Ng, m = s->mix_m;
   const int64_t n = s->ne * (int64_t)s->Nst;
+  if (!s->fcgP && (e = dev_alloc(s, (void**)&s->fcgP, (size_t)m * n * sizeof(double))) != STDG_OK) return e;
+  if (!s->fcgQ && (e = dev_alloc(s, (void**)&s->fcgQ, (size_t)m * n * sizeof(double))) != STDG_OK) return e;
   LpKernels lk = lp_kernels();
   double Tpd[kMaxNg * kMaxNg];
   TpArg Tp{}, Tpinv{};
@@ -805,19 +1033,18 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   double* rz = s->scal; double* pq = s->scal + 8; double* alpha = s->scal + 16; double* beta = s->scal + 24;
   double* rrnew = s->scal + 32; double* res = s->scal + 48; double* rznew = s->scal + 56;
   double* flag = s->scal + 96;                            // breakdown of the binary32 recurrence
-  // outer (binary64) scalars
-  double* o_zq = s->scal + 400; double* o_pq = s->scal + 408; double* o_pqp = s->scal + 416;
-  double* o_rp = s->scal + 424; double* o_al = s->scal + 432; double* o_be = s->scal + 440;
-  double* o_rr = s->scal + 448;                           // Ng column r.r, then ||(I (x) Tp) r||^2
-  double* r = s->kr; double* p = s->kp; double* q = s->kq; double* z = s->kz; double* rhs = s->kb;
+  // outer (binary64) scalars: m x Ng dots z.Q_j, P_j.Q_j, coefficients; Ng-wide rest
+  double* o_rp = s->scal + 400; double* o_al = s->scal + 408; double* o_rr = s->scal + 416;
+  double* o_zq = s->scal + 500; double* o_pqs = s->scal + 600; double* o_c = s->scal + 700;   // m * Ng <= 80 each
+  double* r = s->kr; double* z = s->kz; double* rhs = s->kb;
   const ApplyArgs S = pressure_op(s, 1, 1, -1.0, 1.0);
-  // B' and r = B' (x = 0)
   ++s->nlaunch;
   k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Tpinv, -1.0, b, rhs);
   cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   double rdec = host_norm(s, r, n);                       // ||r|| of the decoupled system
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
+    (void)slot;
     if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
     cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
     if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
@@ -826,19 +1053,19 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
     k_cg_alpha_guard<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha, flag);
     lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tpd, s->part);
-    k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, rrnew);
     lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
     k_cg_beta_guard<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng, flag);
     lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
-    cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     return STDG_OK;
   };
   const int kin = s->mix_inner;
+  GraphLoop inner;
+  const bool use_graph = s->opt.graph_batch > 1;
+  if (use_graph && (e = graph_capture(s, kin, body, inner)) != STDG_OK) return e;
   int total = 0, it = 0;
   double rfull = bn;
-  while (true) {
-    if (total >= s->opt.max_iters) break;
+  while (total < s->opt.max_iters && it < 100000) {
     // ---- preconditioner: kin binary32 block-Jacobi CG iterations on S d = r / ||r||, d0 = 0
     lk.f32s(s->stream, n, 1.0 / rdec, r, s->fr);
     cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
@@ -847,44 +1074,45 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
     cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
     s->nlaunch += 3;
-    int done_it = 0;
-    double est = 0.0;
-    if (s->opt.graph_batch > 1) {
-      e = run_batched(s, kin, 10, kin, -1.0, body, &done_it, &est, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2);
-      if (e != STDG_OK && e != STDG_ENAN) return e;
+    if (use_graph) {
+      if ((e = graph_launch(s, inner, 9, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
     } else {
-      for (; done_it < kin; ++done_it) {
-        if ((e = body(0, nullptr)) != STDG_OK) return e;
-        s->nlaunch += 10; ++s->op_launches;
+      for (int j = 0; j < kin; ++j) {
+        if ((e = body(j, nullptr)) != STDG_OK) return e;
+        s->nlaunch += 9; ++s->op_launches;
       }
     }
-    total += done_it;
+    total += kin;
     // z = ||r|| d in binary64
     cudaMemsetAsync(z, 0, n * sizeof(double), s->stream);
     lk.accum(s->stream, n, rdec, s->fx, z);
-    ++s->nlaunch;
-    // ---- flexible CG step: p = z - (z.Sp_prev / p_prev.Sp_prev) p_prev (per column)
-    if (it == 0) {
+    // ---- flexible CG step: p = z - Sum_j (z.Q_j / P_j.Q_j) P_j over the stored directions
+    const int slot = it % m, used = it < m ? it : m;
+    double* p = s->fcgP + (size_t)slot * n;
+    double* q = s->fcgQ + (size_t)slot * n;
+    if (used == 0) {
       cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
     } else {
-      k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, z, q, s->part);
-      k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, o_zq);
-      k_fcg_beta<<<1, 32, 0, s->stream>>>(Ng, o_zq, o_pqp, o_be);
-      k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, o_be, z, p);
+      k_fcg_dots<<<dim3(kRedBlocks, used), kRedThreads, 0, s->stream>>>(n, N, Ng, used, s->fcgQ, z, s->part);
+      k_final<<<used * Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, used * Ng, s->part, o_zq);
+      k_fcg_coef<<<1, 64, 0, s->stream>>>(used * Ng, o_zq, o_pqs, o_c);
+      // the slot being overwritten is excluded: when the ring is full its coefficient is set to 0
+      if (used == m) cudaMemsetAsync(o_c + slot * Ng, 0, Ng * sizeof(double), s->stream);
+      k_fcg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, used, o_c, s->fcgP, z, s->kp);
+      cudaMemcpyAsync(p, s->kp, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
       s->nlaunch += 4;
     }
     e = op_apply(s, S, p, q);
     if (e != STDG_OK) return e;
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, p, q, s->part);
-    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, o_pq);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, o_pqs + slot * Ng);
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, p, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, o_rp);
-    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, o_rp, o_pq, o_al);
+    k_cg_alpha<<<1, 32, 0, s->stream>>>(Ng, o_rp, o_pqs + slot * Ng, o_al);
     k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, o_al, x, r, p, q, Tp, s->part);
     k_final<<<Ng + 1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, s->part, o_rr);
-    cudaMemcpyAsync(o_pqp, o_pq, Ng * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
     cudaMemcpyAsync(s->hostbuf + 880, o_rr, (Ng + 1) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    s->nlaunch += 8;
+    s->nlaunch += 9;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("mixed solve: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
     ++it;
     double rr = 0.0;
@@ -893,7 +1121,6 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     rfull = std::sqrt(s->hostbuf[880 + Ng]);
     if (!std::isfinite(rfull)) { set_error("mixed solve: non-finite residual"); return STDG_ENAN; }
     if (rfull <= tol * bn || rdec == 0.0) break;
-    if (it >= 2000) break;
   }
   int herr = 0;
   cudaMemcpy(&herr, s->derr, sizeof(int), cudaMemcpyDeviceToHost);
@@ -993,7 +1220,10 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
     I.v[0] = 1.0;
     return cg_block(s, a, b, x, false, I, tol * bn, iters, res);
   }
-  return gmres(s, a, b, x, false, tol * bn, iters, &rs, res);
+  // GMRES with a short restart: the system is well conditioned (a few tens of iterations from the
+  // previous Picard iterate), and the classical Gram-Schmidt passes against up to m basis vectors
+  // cost as much as the operator itself at m ~ 25, so m = 20 bounds that work
+  return gmres(s, a, b, x, false, tol * bn, iters, &rs, res, std::min(20, s->opt.restart));
 }
 
 // ---------------------------------------------------------------------------------------------

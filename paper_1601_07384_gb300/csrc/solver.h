@@ -53,7 +53,9 @@ struct stdg_solver {
   void *wdBv = nullptr;                       // same for the viscous diagonal blocks B_i - Bvisc_i
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
-  int mix_inner = 50;                         // binary32 CG iterations per outer step of the mixed solve
+  int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
+  int mix_m = 16;                             // directions the outer flexible CG keeps
+  double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
   float *fr = nullptr, *fp = nullptr, *fq = nullptr, *fz = nullptr, *fx = nullptr, *fb = nullptr;
   double* dmix = nullptr;                     // device copy of K (time mixing)
@@ -96,6 +98,10 @@ struct stdg_solver {
   double kind_ms[4] = {0, 0, 0, 0};           // by kernel kind: FP64, pair-FP32, FP32, BF16
   int64_t kind_n[4] = {0, 0, 0, 0};
   int ev_kind[4096];
+  // stdg_step phase timing (profiling): event pool, the phase each recorded event closes, totals
+  std::vector<cudaEvent_t> phase_ev;
+  std::vector<int> phase_of;
+  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace stdg {

@@ -529,6 +529,30 @@ extern "C" stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* f) {
   return STDG_OK;
 }
 
+// Profiling: an event on the solver's stream closing `phase` (-1: the start mark of a step).
+static void phase_mark(stdg_solver* s, int phase) {
+  if (!s->prof) return;
+  if (s->phase_ev.empty()) {
+    s->phase_ev.assign(64, nullptr);
+    for (auto& e : s->phase_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; }
+  }
+  const size_t k = s->phase_of.size();
+  if (k >= s->phase_ev.size() || !s->phase_ev[k]) return;
+  cudaEventRecord(s->phase_ev[k], s->stream);
+  s->phase_of.push_back(phase);
+}
+static void phase_fold(stdg_solver* s) {
+  if (s->phase_of.size() < 2) { s->phase_of.clear(); return; }
+  cudaEventSynchronize(s->phase_ev[s->phase_of.size() - 1]);
+  for (size_t k = 1; k < s->phase_of.size(); ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->phase_ev[k - 1], s->phase_ev[k]) == cudaSuccess && s->phase_of[k] >= 0)
+      s->phase_ms[s->phase_of[k]] += ms;
+  }
+  s->phase_of.clear();
+}
+
 extern "C" stdg_status stdg_set_theta(stdg_solver* s, double theta) {
   if (!s || !(theta >= 0.5 && theta <= 1.0)) { set_error("stdg_set_theta: theta must lie in [1/2, 1]"); return STDG_EINVAL; }
   if (theta != 1.0 && s->pt != 0) { set_error("stdg_set_theta: the theta method needs p_t = 0"); return STDG_EINVAL; }
@@ -552,6 +576,8 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   for (int a = 0; a < Ng; ++a) { g0.v[a] = s->g0[a]; g1.v[a] = s->g1[a]; }
   for (int q = 0; q < Ng * Ng; ++q) { K.v[q] = s->K[q]; Ki.v[q] = s->Kinv[q]; }
   stdg_step_stats local{};
+  s->phase_of.clear();
+  phase_mark(s, -1);
   // previous slab average and new-slab boundary data
   ++s->nlaunch;
   k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar_n);
@@ -569,6 +595,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   cudaMemsetAsync(s->P, 0, np * sizeof(double), st);
   const size_t conv_smem = ((size_t)9 * Nst + 64 * 9) * sizeof(double);
   cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+  phase_mark(s, 0);
   for (int k = 0; k < n_picard; ++k) {
     // 1. averaging and previous-Picard pressure gradient
     ++s->nlaunch;
@@ -584,6 +611,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), st>>>(N, Ng, s->dm.left, s->dm.right, s->Q, Plam, s->dt, Ki, s->F);
     ++s->nlaunch;
     k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->F, s->Lam);
+    phase_mark(s, 1);
     // 2. convection
     ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
                 s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
@@ -591,6 +619,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
                 s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, to_arg(s->bc), s->t, s->dt, s->Vbar, s->Ups};
     ++s->nlaunch;
     k_convection<<<ne, 128, conv_smem, st>>>(ca);
+    phase_mark(s, 2);
     // 3. viscous systems (Eq. A1_mod), one per component, initial guess vbar^{n+1,k}
     ++s->nlaunch;
     k_visc_rhs<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.t2n, s->dm.detJ, s->Q, g0, g1, K, nu, s->Vbar_n,
@@ -604,6 +633,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
       if (e != STDG_OK) return e;
       vits += it;
     }
+    phase_mark(s, 3);
     // 4. goback
     ++s->nlaunch;
     k_goback<<<nf, 128, 0, st>>>(ne, N, Ng, s->dm.left, s->dm.right, s->Mij, s->Vbar, s->Vbc, s->F);
@@ -618,8 +648,10 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
       if (e != STDG_OK) return e;
     }
     stdg_solve_stats ss{};
+    phase_mark(s, 4);
     e = solve_pressure(s, s->bvec, s->dp, tol, method, &ss);
     if (e != STDG_OK) return e;
+    phase_mark(s, 5);
     ++s->nlaunch;
     k_axpy<<<1216, 256, 0, st>>>(np, 1.0 / th, s->dp, s->P);     // dp is the increment of p^{n+theta}
     // 6. velocity update (Eq. A3_mod)
@@ -627,6 +659,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     if (launch_update(nf, N, Ng, s->dm.left, s->dm.right, s->Q, s->F, s->dp, s->dt, s->Kinv.data(), s->V, st) != cudaSuccess) {
       set_error("update launch failed"); return STDG_ECUDA;
     }
+    phase_mark(s, 6);
     local.press_iters[k] = ss.iterations;
     local.fallbacks += ss.fallback;
     local.press_residual[k] = ss.rel_residual;
@@ -640,7 +673,9 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   k_maxabs<<<256, 256, 0, st>>>(np, Nst, s->bvec, s->part);
   std::vector<double> part(256);
   cudaMemcpyAsync(s->hostbuf + 512, s->part, 256 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  phase_mark(s, 6);
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("step failed: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+  phase_fold(s);
   double mx = 0.0;
   for (int q = 0; q < 256; ++q) mx = std::fmax(mx, s->hostbuf[512 + q]);
   local.max_divergence = mx;
