@@ -40,6 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk 
 DF_OPS_PER_TERM = 12
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / DF_OPS_PER_TERM * 2 / 1e12
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
+RESTART = 6          # steps from the initial state before the run restarts from it (see advance())
 
 
 def nbasis(p):
@@ -310,8 +311,23 @@ def main():
     if args.theta != 1.0:
         solver.set_theta(args.theta)
     stream = solver.stream
+    # At dt = 0.005 on this mesh (convective CFL of the DG scheme about 2) the time stepping is
+    # unstable: it stays bounded to t = 0.04 and diverges from step 9 on.  The configured dt is kept,
+    # and the run restarts from the initial state every RESTART steps (a device-to-device state
+    # copy, inside the timed region when it falls there), so any --steps/--warmup stay in range.
+    S0 = solver.get_state()
+    since = [0]
+
+    def advance():
+        if since[0] == RESTART:
+            solver.set_state(*S0)
+            since[0] = 0
+        since[0] += 1
+        return solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
+
     for _ in range(args.warmup):
-        solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
+        advance()
+    Pw, Vw, tw = solver.get_state()          # the timed steps' starting state (reused end to end)
 
     def barrier():
         if world > 1:
@@ -326,7 +342,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            stats.append(solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"]))
+            stats.append(advance())
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
@@ -339,18 +355,21 @@ def main():
     # whole job: replicas each run K steps of the same workload; s/step over all steps of all ranks
     s_per_step = ms / 1e3 / (args.steps * world)
 
-    # ---- end to end through the C ABI with host buffers (state in from / out to pinned host memory)
+    # ---- end to end through the C ABI with host buffers: every step copies its input state from
+    # pinned host memory and its result back; each repeats a timed step (same input state), so the
+    # run covers the same simulated interval as the timed region
     P0, V0, t0 = solver.get_state()
+    Pin = torch.empty(Pw.numel(), dtype=torch.float64).pin_memory(); Pin.copy_(Pw)
+    Vin = torch.empty(Vw.numel(), dtype=torch.float64).pin_memory(); Vin.copy_(Vw)
     Ph = torch.empty(P0.numel(), dtype=torch.float64).pin_memory()
     Vh = torch.empty(V0.numel(), dtype=torch.float64).pin_memory()
-    Ph.copy_(P0); Vh.copy_(V0)
     lib = g._lib.load()
     import ctypes as C
-    tcur = C.c_double(t0)
+    tcur = C.c_double(tw)
     barrier()
     te0 = time.perf_counter()
     for _ in range(args.steps):
-        g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0, tcur.value))
+        g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Pin.data_ptr()), C.c_void_p(Vin.data_ptr()), 0, tw))
         solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
         g._lib.check(lib.stdg_get_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0,
                                         C.byref(tcur)))
@@ -360,10 +379,10 @@ def main():
     # ---- the paper's plain FP64 solver on the same step (GMRES(50); CG when p_t = 0), same state
     gm = None
     if args.gmres_steps > 0:
-        solver.set_state(P0, V0, t0)
+        solver.set_state(Pw, Vw, tw)
         gsolver = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=args.gmres_max_iters)
         gsolver.set_boundary(fld)
-        gsolver.set_state(P0, V0, t0)
+        gsolver.set_state(Pw, Vw, tw)
         if args.theta != 1.0:
             gsolver.set_theta(args.theta)
         plain = "cg" if w["pt"] == 0 else "gmres"      # the paper's solver: CG when p_t = 0
@@ -433,6 +452,8 @@ def main():
                                        "mixed_f32": "f64 outer (pair products) / f32 inner", "mixed_bf16": "f64 outer (pair products) / bf16 inner"}[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_name(w) + (f", theta={args.theta}" if args.theta != 1.0 else ""),
+                   "steps": f"restarted from the initial state every {RESTART} steps (t <= {RESTART * w['dt']:g}): "
+                            f"the scheme diverges from step 9 at this dt",
                    "solver": args.solver, "precision": args.precision,
                    "parallelism": f"replicas only: {world} independent copies" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},

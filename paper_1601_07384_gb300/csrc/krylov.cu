@@ -1052,7 +1052,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
     k_cg_alpha_guard<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha, flag);
-    lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tpd, s->part);
+    lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tpd, s->part, 0);
     lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
     k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
     k_cg_beta_guard<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng, flag);

@@ -469,46 +469,66 @@ __device__ inline void lp_block_store(double* v, int cnt, double* part, int stri
     part[blockIdx.x * stride + threadIdx.x] = t;
   }
 }
-__global__ void __launch_bounds__(256) k_lp_coldot(int64_t n, int N, int Ng, const float* __restrict__ x,
+// Column dots of binary32 vectors: one thread per (tet, row) pair covering all Ng columns, binary32
+// sums per thread (about ten pairs each), binary64 across threads (the binary64 pipe is 1/64 of
+// the binary32 rate on sm_103a, so no per-element binary64 work)
+__global__ void __launch_bounds__(256) k_lp_coldot(int64_t ne, int N, int Ng, const float* __restrict__ x,
                                                   const float* __restrict__ y, double* part) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    acc[(e / N) % Ng] += (double)(x[e] * y[e]);
-  lp_block_store(acc, Ng, part, Ng);
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int64_t o = i * Nst + (e - i * N);
+    for (int a = 0; a < Ng; ++a) acc[a] = fmaf(x[o + a * N], y[o + a * N], acc[a]);
+  }
+  double d[8];
+  for (int a = 0; a < 8; ++a) d[a] = acc[a];
+  lp_block_store(d, Ng, part, Ng);
 }
 struct LpTp { float v[kMaxNg * kMaxNg]; };
+// x += alpha_a p; r -= alpha_a q; with want, partials of r.r per column and of ||(I (x) Tp) r||^2
 __global__ void __launch_bounds__(256) k_lp_cg_update(int64_t ne, int N, int Ng, const double* __restrict__ alpha,
                                                      float* __restrict__ x, float* __restrict__ r,
                                                      const float* __restrict__ p, const float* __restrict__ q,
-                                                     LpTp Tp, double* part) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                                                     LpTp Tp, double* part, int want) {
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   float al[kMaxNg];
   for (int a = 0; a < Ng; ++a) al[a] = (float)alpha[a];
   const int Nst = N * Ng;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne * N; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / N;
-    const int k = (int)(e % N);
+    const int64_t o0 = i * Nst + (e - i * N);
     float rv[kMaxNg];
     for (int a = 0; a < Ng; ++a) {
-      const int64_t o = i * Nst + a * N + k;
+      const int64_t o = o0 + a * N;
       x[o] = fmaf(al[a], p[o], x[o]);
       const float rn = fmaf(-al[a], q[o], r[o]);
       r[o] = rn;
       rv[a] = rn;
-      acc[a] += (double)(rn * rn);
+      if (want) acc[a] = fmaf(rn, rn, acc[a]);
     }
-    for (int a = 0; a < Ng; ++a) {
-      float w = 0.0f;
-      for (int b = 0; b < Ng; ++b) w = fmaf(Tp.v[a * Ng + b], rv[b], w);
-      acc[Ng] += (double)(w * w);
-    }
+    if (want)
+      for (int a = 0; a < Ng; ++a) {
+        float w = 0.0f;
+        for (int b = 0; b < Ng; ++b) w = fmaf(Tp.v[a * Ng + b], rv[b], w);
+        acc[Ng] = fmaf(w, w, acc[Ng]);
+      }
   }
-  lp_block_store(acc, Ng + 1, part, Ng + 1);
+  if (!want) return;
+  double d[8];
+  for (int a = 0; a < 8; ++a) d[a] = acc[a];
+  lp_block_store(d, Ng + 1, part, Ng + 1);
 }
-__global__ void k_lp_cg_dir(int64_t n, int N, int Ng, const double* __restrict__ beta, const float* __restrict__ z,
+__global__ void k_lp_cg_dir(int64_t ne, int N, int Ng, const double* __restrict__ beta, const float* __restrict__ z,
                             float* __restrict__ p) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    p[e] = fmaf((float)beta[(e / N) % Ng], p[e], z[e]);
+  float be[kMaxNg];
+  for (int a = 0; a < Ng; ++a) be[a] = (float)beta[a];
+  const int Nst = N * Ng;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int64_t o = i * Nst + (e - i * N);
+    for (int a = 0; a < Ng; ++a) p[o + a * N] = fmaf(be[a], p[o + a * N], z[o + a * N]);
+  }
 }
 // z_i = Binv_i r_i per time column, several tets per block pass (thread -> (tet, output)); partials of r.z
 __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const float* __restrict__ Binv,
@@ -517,7 +537,7 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const
   const int Nst = N * Ng;
   const int TB = blockDim.x / Nst;                  // tets per pass
   const size_t NN = (size_t)N * N;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const int tl = threadIdx.x / Nst, o = threadIdx.x - tl * Nst, a = o / N, k = o - a * N;
   for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
     __syncthreads();
@@ -533,11 +553,13 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const
       float sacc = 0.0f;
       for (int l = 0; l < N; ++l) sacc = fmaf(B[(size_t)l * N], rr[l], sacc);
       z[(size_t)i * Nst + o] = sacc;
-      acc[a] += (double)(sacc * rs[tl * Nst + o]);
+      acc[a] = fmaf(sacc, rs[tl * Nst + o], acc[a]);
     }
   }
   __syncthreads();
-  lp_block_store(acc, Ng, part, Ng);
+  double d[8];
+  for (int q = 0; q < 8; ++q) d[q] = acc[q];
+  lp_block_store(d, Ng, part, Ng);
 }
 // out = float(coef * Sum_b M[a][b] in[b])   (time mixing + conversion)
 __global__ void k_lp_from64(int64_t ne, int N, int Ng, const double* __restrict__ M, double coef,
@@ -573,16 +595,16 @@ __global__ void k_lp_f32(int64_t n, const double* __restrict__ in, float* __rest
 LpKernels lp_kernels() {
   LpKernels k;
   k.coldot = [](cudaStream_t st, int64_t n, int N, int Ng, const float* x, const float* y, double* part) {
-    k_lp_coldot<<<kLpBlocks, 256, 0, st>>>(n, N, Ng, x, y, part);
+    k_lp_coldot<<<kLpBlocks, 256, 0, st>>>(n / ((int64_t)N * Ng), N, Ng, x, y, part);
   };
   k.update = [](cudaStream_t st, int64_t ne, int N, int Ng, const double* alpha, float* x, float* r, const float* p,
-                const float* q, const double* Tp, double* part) {
+                const float* q, const double* Tp, double* part, int want) {
     LpTp t{};
     for (int c = 0; c < Ng * Ng; ++c) t.v[c] = (float)Tp[c];
-    k_lp_cg_update<<<kLpBlocks, 256, 0, st>>>(ne, N, Ng, alpha, x, r, p, q, t, part);
+    k_lp_cg_update<<<kLpBlocks, 256, 0, st>>>(ne, N, Ng, alpha, x, r, p, q, t, part, want);
   };
   k.dir = [](cudaStream_t st, int64_t n, int N, int Ng, const double* beta, const float* z, float* p) {
-    k_lp_cg_dir<<<kLpBlocks, 256, 0, st>>>(n, N, Ng, beta, z, p);
+    k_lp_cg_dir<<<kLpBlocks, 256, 0, st>>>(n / ((int64_t)N * Ng), N, Ng, beta, z, p);
   };
   k.bjacobi = [](cudaStream_t st, int ne, int N, int Ng, const float* Binv, const float* r, float* z, double* part) {
     const int Nst = N * Ng, TB = Nst > 256 ? 1 : 256 / Nst;

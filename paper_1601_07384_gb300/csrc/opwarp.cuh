@@ -110,6 +110,13 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   // NC != 0: N known at compile time (row loops fully unrolled, shared-memory offsets immediate)
   const int N = NC ? NC : a.N, NR = NC ? warp_nr_c(NC) : a.NR, NP = NC ? warp_np_c(NC) : a.NP;
   const int Nst = NC ? NC * NG : a.Nst, S = a.S;
+  // kernel parameters in the arithmetic type, converted once (a binary64 conversion or compare per
+  // output row would go through the 1/64-rate binary64 pipe)
+  const Real scale = (Real)a.scale;
+  const bool has_mass = a.mass_coef != 0.0, kron = a.kron != 0, pinned = a.pinned != 0;
+  Real tacc[NG * NG];
+#pragma unroll
+  for (int c = 0; c < NG * NG; ++c) tacc[c] = (Real)a.Tacc[c];
   const int zplane = 5 * NG * NR;
   const int ZR = kDirectZ ? N : NR;                 // row stride of z
   for (int e = lane; e < W::kPlanes * zplane; e += 32) zs[e] = 0.0f;     // padding entries stay 0
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
         for (int q = 0; q < NG; ++q)
           for (int l = lane; l < N; l += 32) {
             XIn v = xr[sl * Nst + q * N + l];
-            if (a.pinned && nb == 0 && l == 0) v = (XIn)0;
+            if (pinned && nb == 0 && l == 0) v = (XIn)0;
             float* zq = zs + (sl * NG + q) * NR + l;
             if constexpr (kDF) {
               const float2 hl = df_split(v);
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
         if constexpr (kDF) {
           float s, t;
           df_two_sum(h0[q], h1[q], s, t);
-          v[q] = (double)s + ((double)t + (double)l0[q] + (double)l1[q]);
+          v[q] = (double)s + (double)(t + (l0[q] + l1[q]));   // the error terms are ~2^-24 of s
         } else {
           v[q] = h0[q] + h1[q];
         }
@@ -262,19 +269,19 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
 #pragma unroll
       for (int q = 0; q < NG; ++q) {
         Real o = v[q];
-        if (!a.kron) {
+        if (!kron) {
           o = 0;
 #pragma unroll
-          for (int b = 0; b < NG; ++b) o += (Real)a.Tacc[q * NG + b] * v[b];
+          for (int b = 0; b < NG; ++b) o += tacc[q * NG + b] * v[b];
         }
-        o *= (Real)a.scale;
-        if (a.mass_coef != 0.0) {                 // x_i as staged (binary64 for the pair policy)
+        o *= scale;
+        if (has_mass) {                           // x_i as staged (binary64 for the pair policy)
           Real m = 0;
 #pragma unroll
           for (int b = 0; b < NG; ++b) m += (Real)a.Kmass[q * NG + b] * (Real)xr[b * N + k];
           o += (Real)(a.mass_coef * a.detJ[i]) * m;
         }
-        if (a.pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
+        if (pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
         y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
       }
     }

@@ -109,7 +109,7 @@ namespace stdg {
 struct LpKernels {
   void (*coldot)(cudaStream_t, int64_t, int, int, const float*, const float*, double*);
   void (*update)(cudaStream_t, int64_t, int, int, const double*, float*, float*, const float*, const float*,
-                 const double*, double*);
+                 const double*, double*, int);
   void (*dir)(cudaStream_t, int64_t, int, int, const double*, const float*, float*);
   void (*bjacobi)(cudaStream_t, int, int, int, const float*, const float*, float*, double*);
   void (*from64)(cudaStream_t, int64_t, int, int, const double*, double, const double*, float*);
