@@ -222,6 +222,32 @@ __global__ void k_cg_alpha_guard(int Ng, const double* rr, const double* pq, dou
   if (a < Ng) alpha[a] = bad ? 0.0 : al;
   if (a == 0 && bad) flag[0] = 1.0;
 }
+// One block: reduce the per-block p.q partials of every column in a fixed order, then the guarded
+// step length of k_cg_alpha_guard (one launch instead of two per binary32 iteration).
+__global__ void k_final_alpha_guard(int nparts, int Ng, const double* __restrict__ part, const double* rz,
+                                    double* alpha, double* flag) {
+  __shared__ double red[kMaxNg][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = 0; a < Ng; ++a) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * Ng + a];
+    s = warp_sum(s);
+    if (lane == 0) red[a][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double al[kMaxNg];
+    bool bad = flag[0] != 0.0;
+    for (int a = 0; a < Ng; ++a) {
+      double pq = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) pq += red[a][q];
+      al[a] = rz[a] / pq;
+      if (!(pq > 0.0) || !isfinite(al[a])) bad = true;
+    }
+    for (int a = 0; a < Ng; ++a) alpha[a] = bad ? 0.0 : al[a];
+    if (bad) flag[0] = 1.0;
+  }
+}
 // k_cg_beta2 for the mixed solve: the residual estimate reads -1 once the recurrence is frozen
 __global__ void k_cg_beta_guard(int Ng, double* rz, const double* rznew, double* beta, double* res, const double* mix2,
                                 const double* flag) {
@@ -1043,19 +1069,20 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   double rdec = host_norm(s, r, n);                       // ||r|| of the decoupled system
+  const int npq = warp_blocks_lp(s);
+  if (npq <= 0) { set_error("binary32 operator not prepared"); return STDG_ECUDA; }
+  if (!s->opdot && (e = dev_alloc(s, (void**)&s->opdot, (size_t)npq * kMaxNg * sizeof(double))) != STDG_OK) return e;
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
     (void)slot;
     if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
-    cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f);
+    // the operator also writes per-block p.q partials, reduced with the step length in one launch
+    cudaError_t ce = launch_apply_lp(s, s->fp, s->fq, 1, 1, -1.0f, 1.0f, s->opdot);
     if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
     if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
-    lk.coldot(s->stream, n, N, Ng, s->fp, s->fq, s->part);
-    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, pq);
-    k_cg_alpha_guard<<<1, 32, 0, s->stream>>>(Ng, rz, pq, alpha, flag);
+    k_final_alpha_guard<<<1, kRedThreads, 0, s->stream>>>(npq, Ng, s->opdot, rz, alpha, flag);
     lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tpd, s->part, 0);
     lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
-    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rznew);
-    k_cg_beta_guard<<<1, 32, 0, s->stream>>>(Ng, rz, rznew, beta, res, rrnew + Ng, flag);
+    k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, beta);
     lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
     return STDG_OK;
   };
@@ -1075,11 +1102,11 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
     s->nlaunch += 3;
     if (use_graph) {
-      if ((e = graph_launch(s, inner, 9, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
+      if ((e = graph_launch(s, inner, 6, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
     } else {
       for (int j = 0; j < kin; ++j) {
         if ((e = body(j, nullptr)) != STDG_OK) return e;
-        s->nlaunch += 9; ++s->op_launches;
+        s->nlaunch += 6; ++s->op_launches;
       }
     }
     total += kin;

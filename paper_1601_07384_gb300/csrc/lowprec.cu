@@ -433,8 +433,10 @@ static cudaError_t launch_tma(stdg_solver* s, const typename Pol::TB* Bd, const 
   }
 }
 
-cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag) {
-  if (s->op_warp) return launch_apply_warp_lp(s, x, y, pinned, kron, scale, pin_diag);
+cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag,
+                            double* dotpart) {
+  if (s->op_warp) return launch_apply_warp_lp(s, x, y, pinned, kron, scale, pin_diag, dotpart);
+  if (dotpart) return cudaErrorNotSupported;      // the block-staged kernels write no dot partials
   if (s->lpkind == STDG_PREC_MIXED_BF16)
     return launch_tma<PolBF16>(s, static_cast<const __nv_bfloat16*>(s->lpB), static_cast<const __nv_bfloat16*>(s->lpA),
                                s->lpSB, x, y, pinned, kron, scale, pin_diag);
@@ -530,15 +532,19 @@ __global__ void k_lp_cg_dir(int64_t ne, int N, int Ng, const double* __restrict_
     for (int a = 0; a < Ng; ++a) p[o + a * N] = fmaf(be[a], p[o + a * N], z[o + a * N]);
   }
 }
-// z_i = Binv_i r_i per time column, several tets per block pass (thread -> (tet, output)); partials of r.z
-__global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const float* __restrict__ Binv,
+// z_i = Binv_i r_i per time column: thread per (tet, row k) covering all Ng columns, so each entry of
+// the (symmetric) binary32 inverse is read once; several tets per block pass; partials of r.z per
+// column.  NC: N at compile time (0: runtime).
+template <int NC>
+__global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int Nrt, int Ng, const float* __restrict__ Binv,
                                                     const float* __restrict__ r, float* __restrict__ z, double* part) {
   extern __shared__ float rs[];
+  const int N = NC ? NC : Nrt;
   const int Nst = N * Ng;
-  const int TB = blockDim.x / Nst;                  // tets per pass
+  const int TB = blockDim.x / N;                    // tets per pass
   const size_t NN = (size_t)N * N;
-  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const int tl = threadIdx.x / Nst, o = threadIdx.x - tl * Nst, a = o / N, k = o - a * N;
+  float acc[kMaxNg] = {0, 0, 0, 0, 0};
+  const int tl = threadIdx.x / N, k = threadIdx.x - tl * N;
   for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < TB * Nst; idx += blockDim.x) {
@@ -549,16 +555,26 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int N, int Ng, const
     const int i = i0 + tl;
     if (tl < TB && i < ne) {
       const float* B = Binv + (size_t)i * NN + k;   // symmetric: column k, coalesced over k
-      const float* rr = rs + tl * Nst + a * N;
-      float sacc = 0.0f;
-      for (int l = 0; l < N; ++l) sacc = fmaf(B[(size_t)l * N], rr[l], sacc);
-      z[(size_t)i * Nst + o] = sacc;
-      acc[a] = fmaf(sacc, rs[tl * Nst + o], acc[a]);
+      const float* rr = rs + tl * Nst;
+      float sa[kMaxNg] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int l = 0; l < N; ++l) {
+        const float b = B[(size_t)l * N];
+#pragma unroll
+        for (int a = 0; a < kMaxNg; ++a)
+          if (a < Ng) sa[a] = fmaf(b, rr[a * N + l], sa[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < kMaxNg; ++a)
+        if (a < Ng) {
+          z[(size_t)i * Nst + a * N + k] = sa[a];
+          acc[a] = fmaf(sa[a], rr[a * N + k], acc[a]);
+        }
     }
   }
   __syncthreads();
-  double d[8];
-  for (int q = 0; q < 8; ++q) d[q] = acc[q];
+  double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < kMaxNg; ++a) d[a] = acc[a];
   lp_block_store(d, Ng, part, Ng);
 }
 // out = float(coef * Sum_b M[a][b] in[b])   (time mixing + conversion)
@@ -607,8 +623,14 @@ LpKernels lp_kernels() {
     k_lp_cg_dir<<<kLpBlocks, 256, 0, st>>>(n / ((int64_t)N * Ng), N, Ng, beta, z, p);
   };
   k.bjacobi = [](cudaStream_t st, int ne, int N, int Ng, const float* Binv, const float* r, float* z, double* part) {
-    const int Nst = N * Ng, TB = Nst > 256 ? 1 : 256 / Nst;
-    k_lp_bjacobi<<<kLpBlocks, TB * Nst > 256 ? Nst : 256, (size_t)TB * Nst * sizeof(float), st>>>(ne, N, Ng, Binv, r, z, part);
+    const int TB = 256 / N;                         // one thread per (tet, row)
+    const size_t smem = (size_t)TB * N * Ng * sizeof(float);
+    switch (N) {
+      case 20: k_lp_bjacobi<20><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, Binv, r, z, part); break;
+      case 35: k_lp_bjacobi<35><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, Binv, r, z, part); break;
+      case 10: k_lp_bjacobi<10><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, Binv, r, z, part); break;
+      default: k_lp_bjacobi<0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, Binv, r, z, part); break;
+    }
   };
   k.from64 = [](cudaStream_t st, int64_t ne, int N, int Ng, const double* Mdev, double coef, const double* in, float* out) {
     k_lp_from64<<<kLpBlocks, 256, 0, st>>>(ne, N, Ng, Mdev, coef, in, out);

@@ -28,6 +28,7 @@ struct WarpArgs {
   const double* detJ;
   double mass_coef;
   double Kmass[kMaxNg * kMaxNg];
+  double* dotpart;              // optional: per block and column, Sum of x_i . y_i over its tets
   int* err;
 };
 
@@ -85,11 +86,11 @@ __device__ __forceinline__ void warp_chunk(const TB* B, int stride, uint32_t pla
       df_fma(h[q], lo[q], bh[1], bl[1], zh.y, zl.y);
       df_fma(h[q], lo[q], bh[2], bl[2], zh.z, zl.z);
       df_fma(h[q], lo[q], bh[3], bl[3], zh.w, zl.w);
-    } else {
+    } else {                                      // two independent chains per chunk (h, lo)
       h[q] = fmaf(bh[0], zh.x, h[q]);
-      h[q] = fmaf(bh[1], zh.y, h[q]);
+      lo[q] = fmaf(bh[1], zh.y, lo[q]);
       h[q] = fmaf(bh[2], zh.z, h[q]);
-      h[q] = fmaf(bh[3], zh.w, h[q]);
+      lo[q] = fmaf(bh[3], zh.w, lo[q]);
     }
   }
 }
@@ -157,6 +158,9 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   };
 
   const int nw = gridDim.x * wpc;
+  float dacc[NG];                                 // x_i . y_i of this lane's rows (dotpart)
+#pragma unroll
+  for (int q = 0; q < NG; ++q) dacc[q] = 0.0f;
   int i = blockIdx.x * wpc + warp;
   const int4 none = make_int4(-1, -1, -1, -1);
   int4 gf_c = none, gn_c = none, gf_n = none, gn_n = none;
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
           df_two_sum(h0[q], h1[q], s, t);
           v[q] = (double)s + (double)(t + (l0[q] + l1[q]));   // the error terms are ~2^-24 of s
         } else {
-          v[q] = h0[q] + h1[q];
+          v[q] = (h0[q] + l0[q]) + (h1[q] + l1[q]);
         }
       }
 #pragma unroll
@@ -283,12 +287,28 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
         }
         if (pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
         y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
+        if (a.dotpart) dacc[q] += (float)((Real)x[(size_t)i * Nst + q * N + k] * o);
       }
     }
     __syncwarp();
     if (S == 1 && inx < a.ne) {                   // one stage: the next tet's copies start now
       gf_c = a.gface[inx]; gn_c = a.gnbr[inx];
       issue(inx, 0, gf_c, gn_c);
+    }
+  }
+  if (a.dotpart) {                                // fixed order: lanes by shuffle, warps by index
+    __shared__ float wdot[4][kMaxNg];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      float v = dacc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wdot[warp][q] = v;
+    }
+    __syncthreads();                              // every warp of the block reaches this point
+    if (threadIdx.x < NG) {
+      double t = 0.0;
+      for (int w = 0; w < wpc; ++w) t += (double)wdot[w][threadIdx.x];
+      a.dotpart[(size_t)blockIdx.x * NG + threadIdx.x] = t;
     }
   }
   if (abort) {
@@ -456,7 +476,7 @@ static cudaError_t launch_warp_ng(stdg_solver* s, const WarpArgs& a, const typen
 template <typename W>
 static cudaError_t launch_warp(stdg_solver* s, const void* Bd, const void* Ao, const typename W::XIn* x,
                                typename W::YOut* y, int pinned, int kron, double scale, double pin_diag,
-                               double mass_coef = 0.0, const double* Kmass = nullptr) {
+                               double mass_coef = 0.0, const double* Kmass = nullptr, double* dotpart = nullptr) {
   if (!Bd) return cudaErrorNotReady;
   WarpArgs a = warp_args<W>(s);
   a.gface = reinterpret_cast<const int4*>(s->gface);
@@ -466,6 +486,7 @@ static cudaError_t launch_warp(stdg_solver* s, const void* Bd, const void* Ao, c
   for (int q = 0; q < s->Ng * s->Ng; ++q) a.Tacc[q] = s->tm.Tp[q];
   a.detJ = s->dm.detJ;
   a.mass_coef = Kmass ? mass_coef : 0.0;
+  a.dotpart = dotpart;
   for (int q = 0; Kmass && q < s->Ng * s->Ng; ++q) a.Kmass[q] = Kmass[q];
   a.err = s->derr;
   switch (s->Ng) {

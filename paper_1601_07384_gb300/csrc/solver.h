@@ -56,6 +56,7 @@ struct stdg_solver {
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_m = 16;                             // directions the outer flexible CG keeps
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
+  double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
   float *fr = nullptr, *fp = nullptr, *fq = nullptr, *fz = nullptr, *fx = nullptr, *fb = nullptr;
   double* dmix = nullptr;                     // device copy of K (time mixing)
@@ -120,10 +121,12 @@ struct LpKernels {
 };
 LpKernels lp_kernels();
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
-cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag);
+cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag,
+                            double* dotpart = nullptr);
 cudaError_t warp_prepare(stdg_solver* s, int precision);   // block copies + launch shape, outside capture
 cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
-                                 float pin_diag);
+                                 float pin_diag, double* dotpart = nullptr);
+int warp_blocks_lp(stdg_solver* s);   // blocks of the binary32 operator launch (dot partials it writes)
 cudaError_t launch_apply_warp_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                                  double pin_diag);
 cudaError_t launch_apply_warp_df_visc(stdg_solver* s, const double* x, double* y, double scale, double mass_coef,
