@@ -33,6 +33,8 @@ WORKLOADS = {
     "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
     "learned": dict(n=6, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
     "theta": dict(n=24, p=3, pt=0, nu=0.01, dt=0.005, npic=2, tol=1e-10, restart=50),
+    # the high-order degrees of the 40^3 configuration (p = p_t = 4, nu = 1e-3, dt = 0.01) on a 12^3 mesh
+    "hi": dict(n=12, p=4, pt=4, nu=1e-3, dt=0.01, npic=3, tol=1e-10, restart=50),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 # binary64-accurate products from binary32 pairs: 12 FP32 lane operations per multiply-add term

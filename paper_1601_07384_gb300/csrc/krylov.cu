@@ -1080,8 +1080,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
     if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
     k_final_alpha_guard<<<1, kRedThreads, 0, s->stream>>>(npq, Ng, s->opdot, rz, alpha, flag);
-    lk.update(s->stream, s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, Tpd, s->part, 0);
-    lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
+    lp_update_bjacobi(s->stream, (int)s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, s->lpBinv, s->fz, s->part);
     k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, beta);
     lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
     return STDG_OK;
@@ -1102,11 +1101,11 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
     s->nlaunch += 3;
     if (use_graph) {
-      if ((e = graph_launch(s, inner, 6, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
+      if ((e = graph_launch(s, inner, 5, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
     } else {
       for (int j = 0; j < kin; ++j) {
         if ((e = body(j, nullptr)) != STDG_OK) return e;
-        s->nlaunch += 6; ++s->op_launches;
+        s->nlaunch += 5; ++s->op_launches;
       }
     }
     total += kin;

@@ -577,6 +577,74 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int Nrt, int Ng, con
   for (int a = 0; a < kMaxNg; ++a) d[a] = acc[a];
   lp_block_store(d, Ng, part, Ng);
 }
+// The update and the preconditioner of one binary32 CG iteration in one pass: x += alpha_a p,
+// r -= alpha_a q (alpha from the device), then z = Binv r from the updated rows kept in shared
+// memory (thread per (tet, row), all columns), and partials of r.z per column.
+template <int NC>
+__global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ng, const double* __restrict__ alpha,
+                                                     float* __restrict__ x, float* __restrict__ r,
+                                                     const float* __restrict__ p, const float* __restrict__ q,
+                                                     const float* __restrict__ Binv, float* __restrict__ z,
+                                                     double* part) {
+  extern __shared__ float rs[];
+  __shared__ float s_al[kMaxNg];
+  if (threadIdx.x < Ng) s_al[threadIdx.x] = (float)alpha[threadIdx.x];
+  const int N = NC ? NC : Nrt;
+  const int Nst = N * Ng;
+  const int TB = blockDim.x / N;
+  const size_t NN = (size_t)N * N;
+  float acc[kMaxNg] = {0, 0, 0, 0, 0};
+  const int tl = threadIdx.x / N, k = threadIdx.x - tl * N;
+  for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TB * Nst; idx += blockDim.x) {
+      if (i0 + idx / Nst >= ne) continue;
+      const size_t g = (size_t)i0 * Nst + idx;
+      const float al = s_al[(idx % Nst) / N];
+      x[g] = fmaf(al, p[g], x[g]);
+      const float rn = fmaf(-al, q[g], r[g]);
+      r[g] = rn;
+      rs[idx] = rn;
+    }
+    __syncthreads();
+    const int i = i0 + tl;
+    if (tl < TB && i < ne) {
+      const float* B = Binv + (size_t)i * NN + k;
+      const float* rr = rs + tl * Nst;
+      float sa[kMaxNg] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int l2 = 0; l2 < N; ++l2) {
+        const float b = B[(size_t)l2 * N];
+#pragma unroll
+        for (int a = 0; a < kMaxNg; ++a)
+          if (a < Ng) sa[a] = fmaf(b, rr[a * N + l2], sa[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < kMaxNg; ++a)
+        if (a < Ng) {
+          z[(size_t)i * Nst + a * N + k] = sa[a];
+          acc[a] = fmaf(sa[a], rr[a * N + k], acc[a]);
+        }
+    }
+  }
+  __syncthreads();
+  double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < kMaxNg; ++a) d[a] = acc[a];
+  lp_block_store(d, Ng, part, Ng);
+}
+
+void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alpha, float* x, float* r, const float* p,
+                       const float* q, const float* Binv, float* z, double* part) {
+  const int TB = 256 / N;
+  const size_t smem = (size_t)TB * N * Ng * sizeof(float);
+  switch (N) {
+    case 20: k_lp_update_bj<20><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
+    case 35: k_lp_update_bj<35><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
+    case 10: k_lp_update_bj<10><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
+    default: k_lp_update_bj<0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
+  }
+}
+
 // out = float(coef * Sum_b M[a][b] in[b])   (time mixing + conversion)
 __global__ void k_lp_from64(int64_t ne, int N, int Ng, const double* __restrict__ M, double coef,
                             const double* __restrict__ in, float* __restrict__ out) {

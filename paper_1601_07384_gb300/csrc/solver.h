@@ -120,6 +120,9 @@ struct LpKernels {
   void (*f32s)(cudaStream_t, int64_t, double, const double*, float*);
 };
 LpKernels lp_kernels();
+// x += alpha p; r -= alpha q; z = Binv r; partials of r.z per column (kLpBlocks partials)
+void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alpha, float* x, float* r, const float* p,
+                       const float* q, const float* Binv, float* z, double* part);
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag,
                             double* dotpart = nullptr);
