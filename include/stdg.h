@@ -81,9 +81,11 @@ enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_
  *  STDG_PREC_FP64   : blocks and arithmetic in binary64.
  *  STDG_PREC_DF32   : binary64 blocks and vectors, products formed in pairs of binary32
  *                     ("double-float", ~48-bit significand) because sm_103a's binary64
- *                     pipe is ~1/58 of its binary32 rate; results agree with STDG_PREC_FP64
- *                     to ~1e-14 relative per operator application.  Used for the pressure and
- *                     the viscous operators inside the solves.
+ *                     pipe is 1/64 of its binary32 rate; results agree with STDG_PREC_FP64
+ *                     to ~1e-14 relative per operator application.  Used for the pressure
+ *                     and the viscous operators inside the solves.  Where that kernel would
+ *                     run fewer than 6 warps per SM (its shared memory per warp grows as N^2:
+ *                     p >= 4), the binary64 kernel serves instead; the results are the same.
  *  STDG_PREC_MIXED_F32 / STDG_PREC_MIXED_BF16 : the Kronecker CG methods run as an inner-outer
  *                     iteration: flexible CG in binary64 (operator as in STDG_PREC_DF32)
  *                     preconditioned by a fixed number of block-Jacobi CG iterations whose

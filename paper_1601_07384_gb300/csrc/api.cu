@@ -170,7 +170,9 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   for (size_t k = 0; k < ex.size(); ++k) mi.e[k] = (unsigned char)ex[k];
   cudaError_t ce = launch_face_blocks(d, t, s->p, s->N, r->nq_lin, r->nqf_lin, mi, s->Q, s->Mij, s->C, s->x0h, s->stream);
   if (ce == cudaSuccess) ce = launch_assemble(d, s->N, s->Q, s->Aoff, s->Bdiag, s->Bvisc, s->stream);
-  if (ce == cudaSuccess && s->opt.precision != STDG_PREC_FP64)      // pair blocks: DF32, and the mixed modes' outer operator
+  // pair blocks (DF32, and the mixed modes' outer and viscous operators), unless the pair kernel would
+  // run fewer than 6 warps per SM at this N, Ng: there the binary64 kernel is faster and serves instead
+  if (ce == cudaSuccess && s->opt.precision != STDG_PREC_FP64 && (!s->op_warp || warp_df_warps_per_sm(s) >= 6))
     ce = s->op_warp ? warp_prepare(s, STDG_PREC_DF32) : df_build_blocks(s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) {

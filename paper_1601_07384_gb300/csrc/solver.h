@@ -126,7 +126,8 @@ void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alp
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag,
                             double* dotpart = nullptr);
-cudaError_t warp_prepare(stdg_solver* s, int precision);   // block copies + launch shape, outside capture
+cudaError_t warp_prepare(stdg_solver* s, int precision);
+int warp_df_warps_per_sm(stdg_solver* s);   // occupancy of the pair kernel at this N, Ng   // block copies + launch shape, outside capture
 cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
                                  float pin_diag, double* dotpart = nullptr);
 int warp_blocks_lp(stdg_solver* s);   // blocks of the binary32 operator launch (dot partials it writes)
