@@ -66,7 +66,17 @@ typedef enum {
  *  STDG_SOLVER_KRON_PCG: STDG_SOLVER_KRON_CG preconditioned by block Jacobi: the exact inverse
  *                      of each tet's N x N diagonal block of the pinned -A_sp (built on first
  *                      use, Cholesky on the device).  The paper uses no preconditioner; this
- *                      changes only the iteration, not the system or its stopping test.      */
+ *                      changes only the iteration, not the system or its stopping test.
+ *  STDG_SOLVER_KRON_MG: STDG_SOLVER_KRON_PCG with an additive coarse correction on the
+ *                      constant mode of every tet: z = Binv r + R^T V (R r), R the constant-mode
+ *                      coefficients (pinned one excluded), V one symmetric V-cycle (a damped
+ *                      Jacobi sweep before and after, exact dense solve on the coarsest level)
+ *                      over nested agglomerates of tets (centroids binned into cubes of the mean
+ *                      hexahedron size, doubled per level) with Galerkin coarse matrices.  The
+ *                      hierarchy is built on first use (host setup, a few device arrays).
+ *                      Same system and stopping test; O(1) iterations in h where block Jacobi
+ *                      needs O(1/h).  With the MIXED precisions it preconditions the inner
+ *                      binary32 iterations.                                                  */
 /*  STDG_SOLVER_FGMRES_BJ / STDG_SOLVER_FGMRES_GNN : flexible GMRES(m) on the full operator,
  *                      right-preconditioned by block Jacobi of the full operator
  *                      (A_ii^-1 = B_i^-1 (x) (dt^2 K^-1)^-1) alone, or, for FGMRES_GNN, with
@@ -75,7 +85,7 @@ typedef enum {
  *                      (stdg_gnn_*); later Arnoldi vectors use block Jacobi.  Needs
  *                      stdg_gnn_init.                                                      */
 enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_SOLVER_KRON_PCG = 3,
-       STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5 };
+       STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5, STDG_SOLVER_KRON_MG = 6 };
 
 /* Precision of the operator blocks used inside the Krylov iteration (stdg_solver_options).
  *  STDG_PREC_FP64   : blocks and arithmetic in binary64.

@@ -7,7 +7,7 @@ LIB_PATH = os.path.join(HERE, "libstdg.so")
 
 STATUS = {0: "STDG_OK", -1: "STDG_EINVAL", -2: "STDG_ENOMEM", -3: "STDG_ECUDA", -4: "STDG_ENOCONV",
           -5: "STDG_EMESH", -6: "STDG_ENAN", -7: "STDG_ETIMEOUT", -8: "STDG_EUNSUPPORTED"}
-SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5}
+SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5, "kron_mg": 6}
 PREC = {"fp64": 0, "df32": 1, "mixed_f32": 2, "mixed_bf16": 3}
 FIELD = {"zero": 0, "constant": 1, "beltrami": 2}
 

@@ -78,7 +78,7 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
     const char* k = std::getenv("STDG_OP_KERNEL");   // "tma": block-staged TMA operator kernels
     s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
     const char* mi = std::getenv("STDG_MIXED_INNER");   // binary32 iterations per outer mixed step
-    if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = std::atoi(mi);
+    if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = s->mix_inner_mg = std::atoi(mi);
     const char* mm = std::getenv("STDG_MIXED_M");       // directions kept by the outer flexible CG
     if (mm && std::atoi(mm) > 0 && std::atoi(mm) <= 16) s->mix_m = std::atoi(mm);
   }
@@ -196,6 +196,8 @@ extern "C" void stdg_solver_destroy(stdg_solver* s) {
   if (s->cstream) cudaStreamDestroy(s->cstream);
   for (void* p : s->allocs) cudaFree(p);
   if (s->hostbuf) cudaFreeHost(s->hostbuf);
+  mg_free(s);
+  delete s->gnn;
   delete s;
 }
 

@@ -15,6 +15,7 @@ namespace stdg {
 constexpr int kRedBlocks = 1216;   // 8 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kMaxCols = 64;
+constexpr int kLpBlocksK = 1216;   // partial rows the binary32 block-Jacobi kernels write (lowprec.cu)
 
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -725,10 +726,11 @@ static stdg_status ensure_block_inverse(stdg_solver* s) {
 }
 
 // Block CG for an operator that is symmetric positive definite on each time column, optionally
-// preconditioned by block Jacobi (precond: per-tet inverses of the pinned diagonal blocks of -A).
+// preconditioned by block Jacobi (precond 1: per-tet inverses of the pinned diagonal blocks of -A), or
+// by block Jacobi plus the agglomeration coarse correction of mg.cu (precond 2).
 // x holds the initial guess unless zero_x0.  Stops when ||(I (x) mix) r|| <= tol_abs.
 static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* rhs, double* x, bool zero_x0,
-                            const TpArg& mix, double tol_abs, int* iters, double* res_abs, bool precond = false) {
+                            const TpArg& mix, double tol_abs, int* iters, double* res_abs, int precond = 0) {
   const int N = s->N, Ng = s->Ng;
   const int64_t n = s->ne * (int64_t)s->Nst;
   double* r = s->kr; double* p = s->kp; double* q = s->kq; double* z = s->kz;
@@ -739,8 +741,13 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   const size_t bj_smem = (size_t)bj_tb * s->Nst * sizeof(float);
   if (precond) {
     stdg_status e = ensure_block_inverse(s);
+    if (e == STDG_OK && precond == 2) e = mg_ensure(s);
     if (e != STDG_OK) return e;
   }
+  // block Jacobi writes kRedBlocks rows of r.z partials, the coarse correction its own rows after them
+  const bool mg = precond == 2;
+  const int nrz = kRedBlocks + (mg ? mg_partial_blocks() : 0);
+  double* mgpart = s->part + (size_t)kRedBlocks * Ng;
   if (zero_x0) {
     cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
     cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
@@ -753,6 +760,7 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
   if (precond) {
     ++s->nlaunch;
     k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
+    if (mg) { mg_apply_f64(s, r, z, mgpart); s->nlaunch += mg_launches(s); }
     cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   } else {
     cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
@@ -760,7 +768,7 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
     k_coldot<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, r, r, s->part);
   }
   ++s->nlaunch;
-  k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
+  k_final<<<Ng, kRedThreads, 0, s->stream>>>(precond ? nrz : kRedBlocks, Ng, s->part, rz);
   // one CG iteration; ends by copying the full-system residual norm to the host.  With the
   // preconditioner, inside a captured batch only the batch's last iteration forms the norm (the
   // host reads only that one), and the step length / beta come from fused reduction kernels.
@@ -777,7 +785,8 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
       k_cg_update<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, alpha, x, r, p, q, mix, s->part, want);
       if (want) k_final_res<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng + 1, Ng, s->part, res);
       k_bjacobi32<<<kRedBlocks, bj_threads, bj_smem, s->stream>>>((int)s->ne, N, Ng, s->lpBinv, r, z, s->part);
-      k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, beta);
+      if (mg) mg_apply_f64(s, r, z, mgpart);
+      k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(nrz, Ng, s->part, rz, beta);
       k_cg_dir<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, N, Ng, beta, z, p);
       if (want) cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
       return STDG_OK;
@@ -791,7 +800,7 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
     cudaMemcpyAsync(s->hostbuf + slot, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     return STDG_OK;
   };
-  const int kpi = precond ? 7 : 8;
+  const int kpi = precond ? 7 + mg_launches(s) : 8;
   int it = 0;
   double rabs = INFINITY;
   const int maxit = s->opt.max_iters;
@@ -1038,14 +1047,18 @@ static stdg_status ensure_lowprec(stdg_solver* s) {
 // S X = B' (S = -A_sp (x) I with the pin, B' = -(I (x) Tp^-1) b), operator applied by the
 // binary64-accurate pair kernel; each new direction is S-orthogonalised against the last m
 // directions (flexible CG, Notay 2000), and x, r and all scalars are binary64, so the binary32 parts
-// change how fast it converges, not the accuracy it reaches.  Preconditioner: s->mix_inner
-// iterations of block-Jacobi CG in binary32 (binary32 or bfloat16 operator, binary32 vectors)
-// started from zero on S d = r / ||r||, captured once per solve as a CUDA graph.  Stops when
-// ||(I (x) Tp) r|| (the full-system residual) <= tol ||b||.
+// change how fast it converges, not the accuracy it reaches.  Preconditioner: a fixed number of
+// block-Jacobi CG iterations in binary32 (binary32 or bfloat16 operator, binary32 vectors) started
+// from zero on S d = r / ||r||, captured once per solve as a CUDA graph: s->mix_inner of them, or,
+// with mg, s->mix_inner_mg with block Jacobi plus the agglomeration coarse correction of mg.cu.
+// Stops when ||(I (x) Tp) r|| (the full-system residual) <= tol ||b||.
 static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, double tol, double bn, int* iters,
-                               int* outer, double* res_abs) {
+                               int* outer, double* res_abs, bool mg) {
   stdg_status e = ensure_lowprec(s);
+  if (e == STDG_OK && mg) e = mg_ensure(s);
   if (e != STDG_OK) return e;
+  const int nrz = kLpBlocksK + (mg ? mg_partial_blocks() : 0);   // r.z partial rows: block Jacobi, coarse
+  const int mgl = mg ? mg_launches(s) : 0;
   const int N = s->N, Ng = s->Ng, m = s->mix_m;
   const int64_t n = s->ne * (int64_t)s->Nst;
   if (!s->fcgP && (e = dev_alloc(s, (void**)&s->fcgP, (size_t)m * n * sizeof(double))) != STDG_OK) return e;
@@ -1081,11 +1094,12 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     if (ce != cudaSuccess) { set_error("low-precision operator launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
     k_final_alpha_guard<<<1, kRedThreads, 0, s->stream>>>(npq, Ng, s->opdot, rz, alpha, flag);
     lp_update_bjacobi(s->stream, (int)s->ne, N, Ng, alpha, s->fx, s->fr, s->fp, s->fq, s->lpBinv, s->fz, s->part);
-    k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz, beta);
+    if (mg) mg_apply_f32(s, s->fr, s->fz, s->part + (size_t)kLpBlocksK * Ng);
+    k_final_beta<<<Ng, kRedThreads, 0, s->stream>>>(nrz, Ng, s->part, rz, beta);
     lk.dir(s->stream, n, N, Ng, beta, s->fz, s->fp);
     return STDG_OK;
   };
-  const int kin = s->mix_inner;
+  const int kin = mg ? s->mix_inner_mg : s->mix_inner;
   GraphLoop inner;
   const bool use_graph = s->opt.graph_batch > 1;
   if (use_graph && (e = graph_capture(s, kin, body, inner)) != STDG_OK) return e;
@@ -1097,15 +1111,16 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
     cudaMemsetAsync(flag, 0, sizeof(double), s->stream);
     lk.bjacobi(s->stream, (int)s->ne, N, Ng, s->lpBinv, s->fr, s->fz, s->part);
-    k_final<<<Ng, kRedThreads, 0, s->stream>>>(kRedBlocks, Ng, s->part, rz);
+    if (mg) mg_apply_f32(s, s->fr, s->fz, s->part + (size_t)kLpBlocksK * Ng);
+    k_final<<<Ng, kRedThreads, 0, s->stream>>>(nrz, Ng, s->part, rz);
     cudaMemcpyAsync(s->fp, s->fz, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
-    s->nlaunch += 3;
+    s->nlaunch += 3 + mgl;
     if (use_graph) {
-      if ((e = graph_launch(s, inner, 5, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
+      if ((e = graph_launch(s, inner, 5 + mgl, s->lpkind == STDG_PREC_MIXED_BF16 ? 3 : 2)) != STDG_OK) return e;
     } else {
       for (int j = 0; j < kin; ++j) {
         if ((e = body(j, nullptr)) != STDG_OK) return e;
-        s->nlaunch += 5; ++s->op_launches;
+        s->nlaunch += 5 + mgl; ++s->op_launches;
       }
     }
     total += kin;
@@ -1196,10 +1211,11 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
       it += it2; rs += rs2;
       if (st) st->fallback = 1;
     }
-  } else if ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG) &&
+  } else if ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG || method == STDG_SOLVER_KRON_MG) &&
              (s->opt.precision == STDG_PREC_MIXED_F32 || s->opt.precision == STDG_PREC_MIXED_BF16)) {
-    r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs);
-  } else if (method == STDG_SOLVER_CG || method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG) {
+    r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs, method == STDG_SOLVER_KRON_MG);
+  } else if (method == STDG_SOLVER_CG || method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG ||
+             method == STDG_SOLVER_KRON_MG) {
     // A = A_sp (x) Tp (pinned):  A x = b  <=>  (-A_sp (x) I) x = -(I (x) Tp^-1) b,  Tp^-1 = K / dt^2;
     // the full residual is b - A x = -(I (x) Tp) r for the CG residual r.
     TpArg Tp{}, Tpinv{};
@@ -1208,7 +1224,7 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
     ++s->nlaunch;
     k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, s->N, s->Ng, Tpinv, -1.0, b, s->kb);
     r = cg_block(s, pressure_op(s, 1, 1, -1.0, 1.0), s->kb, x, true, Tp, tol * bn, &it, &rabs,
-                 method == STDG_SOLVER_KRON_PCG);
+                 method == STDG_SOLVER_KRON_PCG ? 1 : method == STDG_SOLVER_KRON_MG ? 2 : 0);
   } else {
     set_error("unknown solver method %d", method);
     return STDG_EINVAL;

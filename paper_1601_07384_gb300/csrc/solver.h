@@ -5,6 +5,7 @@
 #include "dev.cuh"
 
 namespace stdg {
+struct MgState;                    // agglomeration coarse correction (mg.cu)
 // State of the learned preconditioner (gnn.cu)
 struct GnnState {
   int H = 64, L = 3, G = 2, F = 0, C = 0, bf16 = 1;
@@ -54,6 +55,7 @@ struct stdg_solver {
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
+  int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
@@ -81,6 +83,7 @@ struct stdg_solver {
   double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
   std::vector<void*> allocs;
   stdg::GnnState* gnn = nullptr;
+  stdg::MgState* mg = nullptr;               // coarse correction of STDG_SOLVER_KRON_MG (built on first use)
   double* kzz = nullptr;                     // FGMRES preconditioned directions
   int snap_every = 0, snap_cap = 0, nsnap = 0;
   int ah_nsnap = 0, ah_every = 0, ah_max = 0;   // harvest pairs from the pressure systems of stdg_step
@@ -126,8 +129,8 @@ void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alp
 cudaError_t lp_build_blocks(stdg_solver* s, int kind);
 cudaError_t launch_apply_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale, float pin_diag,
                             double* dotpart = nullptr);
-cudaError_t warp_prepare(stdg_solver* s, int precision);
-int warp_df_warps_per_sm(stdg_solver* s);   // occupancy of the pair kernel at this N, Ng   // block copies + launch shape, outside capture
+cudaError_t warp_prepare(stdg_solver* s, int precision);   // block copies + launch shape, outside capture
+int warp_df_warps_per_sm(stdg_solver* s);                  // resident warps per SM of the pair kernel
 cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
                                  float pin_diag, double* dotpart = nullptr);
 int warp_blocks_lp(stdg_solver* s);   // blocks of the binary32 operator launch (dot partials it writes)
@@ -149,5 +152,14 @@ stdg_status gnn_precond(stdg_solver* s, const double* r, double* z, int use_gnn)
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res);
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes);
+// Agglomeration coarse correction (mg.cu): z += R^T V (R r) on the constant modes of every tet, with
+// partials of r.(R^T V R r) per column written to part[b * Ng + a], b < mg_partial_blocks().
+stdg_status mg_ensure(stdg_solver* s);       // host + device setup, outside stream capture
+void mg_apply_f32(stdg_solver* s, const float* r, float* z, double* part);
+void mg_apply_f64(stdg_solver* s, const double* r, double* z, double* part);
+int mg_launches(const stdg_solver* s);       // kernel launches per application
+int mg_partial_blocks();
+int mg_levels(const stdg_solver* s, int* sizes, int cap);
+void mg_free(stdg_solver* s);
 void prof_fold(stdg_solver* s);
 }  // namespace stdg
