@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -830,11 +831,17 @@ static stdg_status cg_block(stdg_solver* s, const ApplyArgs& op, const double* r
 
 // Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations on the host.
 // x holds the initial guess unless zero_x0.  Stops when ||b - A x|| <= tol_abs.
+// Restarted GMRES(m).  With pc_nu >= 0 it is right-preconditioned by the viscous block Jacobi of
+// viscpc.cu (viscosity pc_nu): Arnoldi on A D^-1, x += D^-1 V y at the end of each cycle; the
+// residual it monitors and returns is still that of A x = b.
 static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, double* x, bool zero_x0,
-                         double tol_abs, int* iters, int* nrestarts, double* res_abs, int restart = 0) {
+                         double tol_abs, int* iters, int* nrestarts, double* res_abs, int restart = 0,
+                         double pc_nu = -1.0) {
   const int m = restart > 0 ? restart : s->opt.restart;
   const int64_t n = s->ne * (int64_t)s->Nst;
+  const bool pc = pc_nu >= 0.0;
   stdg_status e = ensure_basis(s, m + 1);
+  if (e == STDG_OK && pc) e = visc_pc_ensure(s);
   if (e != STDG_OK) return e;
   if (zero_x0) cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
@@ -859,7 +866,12 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
     int k = 0;
     for (k = 0; k < m; ++k) {
       double* w = s->basis + (size_t)(k + 1) * n;
-      e = op_apply(s, op, s->basis + (size_t)k * n, w);
+      if (pc) {
+        if ((e = visc_pc_apply(s, pc_nu, s->basis + (size_t)k * n, s->kz, 0)) != STDG_OK) return e;
+        e = op_apply(s, op, s->kz, w);
+      } else {
+        e = op_apply(s, op, s->basis + (size_t)k * n, w);
+      }
       if (e != STDG_OK) return e;
       // classical Gram-Schmidt, second pass only when the first cancelled (gate at hd[260])
       k_sumsq<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, w, s->part);
@@ -908,7 +920,13 @@ static stdg_status gmres(stdg_solver* s, const ApplyArgs& op, const double* b, d
     std::memcpy(s->hostbuf, y.data(), k * sizeof(double));
     cudaMemcpyAsync(hd, s->hostbuf, k * sizeof(double), cudaMemcpyHostToDevice, s->stream);
     ++s->nlaunch;
-    k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k, s->basis, hd, 1.0, x);
+    if (pc) {
+      cudaMemsetAsync(s->kp, 0, n * sizeof(double), s->stream);
+      k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k, s->basis, hd, 1.0, s->kp);
+      if ((e = visc_pc_apply(s, pc_nu, s->kp, x, 1)) != STDG_OK) return e;
+    } else {
+      k_multiaxpy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, k, s->basis, hd, 1.0, x);
+    }
     ++restarts;
   }
   *iters = it; *nrestarts = restarts; *res_abs = beta;
@@ -1262,10 +1280,12 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
     I.v[0] = 1.0;
     return cg_block(s, a, b, x, false, I, tol * bn, iters, res);
   }
-  // GMRES with a short restart: the system is well conditioned (a few tens of iterations from the
-  // previous Picard iterate), and the classical Gram-Schmidt passes against up to m basis vectors
-  // cost as much as the operator itself at m ~ 25, so m = 20 bounds that work
-  return gmres(s, a, b, x, false, tol * bn, iters, &rs, res, std::min(20, s->opt.restart));
+  // GMRES with a short restart, right-preconditioned by the exact inverse of every tet's diagonal
+  // block: the system is mass-dominated and well conditioned, and the classical Gram-Schmidt passes
+  // against up to m basis vectors cost as much as the operator itself at m ~ 25, so m = 20 bounds
+  // that work.  STDG_VISC_PC=0 in the environment selects plain GMRES.
+  static const bool use_pc = !(std::getenv("STDG_VISC_PC") && std::atoi(std::getenv("STDG_VISC_PC")) == 0);
+  return gmres(s, a, b, x, false, tol * bn, iters, &rs, res, std::min(20, s->opt.restart), use_pc ? nu : -1.0);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -84,6 +84,7 @@ struct stdg_solver {
   std::vector<void*> allocs;
   stdg::GnnState* gnn = nullptr;
   stdg::MgState* mg = nullptr;               // coarse correction of STDG_SOLVER_KRON_MG (built on first use)
+  float *vpcU = nullptr, *vpcLam = nullptr;  // viscous block-Jacobi by fast diagonalisation (viscpc.cu)
   double* kzz = nullptr;                     // FGMRES preconditioned directions
   int snap_every = 0, snap_cap = 0, nsnap = 0;
   int ah_nsnap = 0, ah_every = 0, ah_max = 0;   // harvest pairs from the pressure systems of stdg_step
@@ -161,5 +162,9 @@ int mg_launches(const stdg_solver* s);       // kernel launches per application
 int mg_partial_blocks();
 int mg_levels(const stdg_solver* s, int* sizes, int cap);
 void mg_free(stdg_solver* s);
+// Viscous block Jacobi (viscpc.cu): eigenvectors / eigenvalues of every tet's spatial viscous block,
+// then z = D^-1 r (accum: z += D^-1 r) with D the tet-diagonal blocks of the viscous operator.
+stdg_status visc_pc_ensure(stdg_solver* s);
+stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum);
 void prof_fold(stdg_solver* s);
 }  // namespace stdg
