@@ -26,74 +26,77 @@ constexpr int kEigWarps = 4;                 // tets per block of the eigensolve
 constexpr int kEigSweeps = 16;               // cyclic sweeps (each annihilates every pair once)
 constexpr int kEigLd = kMaxN + 1;
 
-// G_i = Bvisc_i - B_i; eigenvectors (columns of U) and eigenvalues, one warp per tet.
+// G_i = Bvisc_i - B_i; eigenvectors (columns of U) and eigenvalues, one warp per tet.  Binary32: the
+// preconditioner needs a fixed approximate inverse, and binary64 rotations on sm_103a's FP64 pipe
+// made this setup ~200 ms at 10,368 tets, p = 4.
 __global__ void __launch_bounds__(32 * kEigWarps) k_visc_eig(int ne, int N, const double* __restrict__ Bdiag,
                                                              const double* __restrict__ Bvisc, float* __restrict__ Uout,
                                                              float* __restrict__ lam) {
-  extern __shared__ double sm[];
+  extern __shared__ float sm[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* A = sm + (size_t)w * 2 * kMaxN * kEigLd;
-  double* V = A + kMaxN * kEigLd;
-  __shared__ double cs_s[kEigWarps][2];
+  float* A = sm + (size_t)w * 2 * kMaxN * kEigLd;
+  float* V = A + kMaxN * kEigLd;
+  __shared__ float cs_s[kEigWarps][2];
   const size_t NN = (size_t)N * N;
   for (int i = blockIdx.x * kEigWarps + w; i < ne; i += gridDim.x * kEigWarps) {
     for (int e = lane; e < N * N; e += 32) {
       const int r = e / N, c = e - r * N;
-      A[r * kEigLd + c] = Bvisc[(size_t)i * NN + e] - Bdiag[(size_t)i * NN + e];
-      V[r * kEigLd + c] = r == c ? 1.0 : 0.0;
+      A[r * kEigLd + c] = (float)(Bvisc[(size_t)i * NN + e] - Bdiag[(size_t)i * NN + e]);
+      V[r * kEigLd + c] = r == c ? 1.0f : 0.0f;
     }
     __syncwarp();
     // symmetrise (the assembled block is symmetric up to rounding)
     for (int e = lane; e < N * N; e += 32) {
       const int r = e / N, c = e - r * N;
       if (r < c) {
-        const double m = 0.5 * (A[r * kEigLd + c] + A[c * kEigLd + r]);
+        const float m = 0.5f * (A[r * kEigLd + c] + A[c * kEigLd + r]);
         A[r * kEigLd + c] = m;
         A[c * kEigLd + r] = m;
       }
     }
     __syncwarp();
     for (int sweep = 0; sweep < kEigSweeps; ++sweep) {
-      double off = 0.0, dia = 0.0;
+      float off = 0.0f, dia = 0.0f;
       for (int e = lane; e < N * N; e += 32) {
         const int r = e / N, c = e - r * N;
-        const double v = A[r * kEigLd + c];
+        const float v = A[r * kEigLd + c];
         if (r != c) off += v * v; else dia += v * v;
       }
       for (int o = 16; o > 0; o >>= 1) {
         off += __shfl_xor_sync(0xffffffffu, off, o);
         dia += __shfl_xor_sync(0xffffffffu, dia, o);
       }
-      if (off <= 1e-28 * dia) break;
+      if (off <= 1e-11f * dia) break;
       for (int p = 0; p < N - 1; ++p)
         for (int q = p + 1; q < N; ++q) {
           if (lane == 0) {
-            const double apq = A[p * kEigLd + q];
-            double c = 1.0, s = 0.0;
-            if (apq != 0.0 && fabs(apq) > 1e-300) {
-              const double tau = (A[q * kEigLd + q] - A[p * kEigLd + p]) / (2.0 * apq);
-              const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-              c = 1.0 / sqrt(1.0 + t * t);
+            const float apq = A[p * kEigLd + q];
+            float c = 1.0f, s = 0.0f;
+            // skip pairs already negligible against their diagonal entries
+            if (fabsf(apq) > 1e-9f * (fabsf(A[p * kEigLd + p]) + fabsf(A[q * kEigLd + q]))) {
+              const float tau = (A[q * kEigLd + q] - A[p * kEigLd + p]) / (2.0f * apq);
+              const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+              c = 1.0f / sqrtf(1.0f + t * t);
               s = t * c;
             }
             cs_s[w][0] = c; cs_s[w][1] = s;
           }
           __syncwarp();
-          const double c = cs_s[w][0], s = cs_s[w][1];
-          if (s != 0.0) {
+          const float c = cs_s[w][0], s = cs_s[w][1];
+          if (s != 0.0f) {
             // A <- A J (columns p, q), V <- V J
             for (int k = lane; k < N; k += 32) {
-              const double akp = A[k * kEigLd + p], akq = A[k * kEigLd + q];
+              const float akp = A[k * kEigLd + p], akq = A[k * kEigLd + q];
               A[k * kEigLd + p] = c * akp - s * akq;
               A[k * kEigLd + q] = s * akp + c * akq;
-              const double vkp = V[k * kEigLd + p], vkq = V[k * kEigLd + q];
+              const float vkp = V[k * kEigLd + p], vkq = V[k * kEigLd + q];
               V[k * kEigLd + p] = c * vkp - s * vkq;
               V[k * kEigLd + q] = s * vkp + c * vkq;
             }
             __syncwarp();
             // A <- J^T A (rows p, q)
             for (int k = lane; k < N; k += 32) {
-              const double apk = A[p * kEigLd + k], aqk = A[q * kEigLd + k];
+              const float apk = A[p * kEigLd + k], aqk = A[q * kEigLd + k];
               A[p * kEigLd + k] = c * apk - s * aqk;
               A[q * kEigLd + k] = s * apk + c * aqk;
             }
@@ -103,23 +106,23 @@ __global__ void __launch_bounds__(32 * kEigWarps) k_visc_eig(int ne, int N, cons
     }
     for (int e = lane; e < N * N; e += 32) {
       const int r = e / N, c = e - r * N;
-      Uout[(size_t)i * NN + e] = (float)V[r * kEigLd + c];     // U[l][k]: row l, eigenvector k
+      Uout[(size_t)i * NN + e] = V[r * kEigLd + c];     // U[l][k]: row l, eigenvector k
     }
-    for (int k = lane; k < N; k += 32) lam[(size_t)i * N + k] = (float)fmax(A[k * kEigLd + k], 0.0);
+    for (int k = lane; k < N; k += 32) lam[(size_t)i * N + k] = fmaxf(A[k * kEigLd + k], 0.0f);
     __syncwarp();
   }
 }
 
-struct SmallK { double v[kMaxNg * kMaxNg]; };
+struct SmallK { float v[kMaxNg * kMaxNg]; };
 
 // z_i = D_i^-1 r_i (accum: z_i += D_i^-1 r_i), thread per (tet, spatial index), all time columns;
-// several tets per block pass with their rows staged in shared memory.  The two products with U run
-// in binary32 (4 N^2 Ng flops per tet would make binary64 FP-pipe-bound on sm_103a); the small
-// solves in binary64.  The result is a fixed linear map of r, as right preconditioning requires.
+// several tets per block pass with their rows staged in shared memory.  All arithmetic is binary32
+// (in binary64 the products and the divides of the small solves are FP64-pipe-bound on sm_103a);
+// the result is a fixed linear map of r, as right preconditioning requires.
 template <int NC>
 __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const float* __restrict__ U,
                                                  const float* __restrict__ lam, const double* __restrict__ detJ,
-                                                 SmallK K, double c, const double* __restrict__ r,
+                                                 SmallK K, float c, const double* __restrict__ r,
                                                  double* __restrict__ z, int accum) {
   extern __shared__ float vs[];
   const int N = NC ? NC : Nrt;
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
       vs[idx] = i0 + idx / Nst < ne ? (float)r[(size_t)i0 * Nst + idx] : 0.0f;
     __syncthreads();
     const int i = i0 + tl;
-    double y[kMaxNg] = {0, 0, 0, 0, 0};
+    float y[kMaxNg] = {0, 0, 0, 0, 0};
     if (tl < TB && i < ne) {
       // w[a] = Sum_l U[l][k] r[a][l]
       const float* Uc = U + (size_t)i * NN + k;
@@ -146,24 +149,22 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
         for (int a = 0; a < kMaxNg; ++a)
           if (a < Ng) wf[a] = fmaf(u, rr[a * N + l], wf[a]);
       }
-      double w[kMaxNg];
-#pragma unroll
-      for (int a = 0; a < kMaxNg; ++a) w[a] = wf[a];
+      float* w = wf;
       // (d K + c lambda_k I) y = w, LU without pivoting
-      const double d = fabs(detJ[i]), cl = c * (double)lam[(size_t)i * N + k];
-      double M[kMaxNg][kMaxNg];
+      const float d = (float)fabs(detJ[i]), cl = c * lam[(size_t)i * N + k];
+      float M[kMaxNg][kMaxNg];
 #pragma unroll
       for (int a = 0; a < kMaxNg; ++a)
 #pragma unroll
-        for (int b = 0; b < kMaxNg; ++b) M[a][b] = (a < Ng && b < Ng) ? d * K.v[a * Ng + b] + (a == b ? cl : 0.0) : 0.0;
+        for (int b = 0; b < kMaxNg; ++b) M[a][b] = (a < Ng && b < Ng) ? d * K.v[a * Ng + b] + (a == b ? cl : 0.0f) : 0.0f;
 #pragma unroll
       for (int p = 0; p < kMaxNg; ++p)
         if (p < Ng) {
-          const double ip = 1.0 / M[p][p];
+          const float ip = 1.0f / M[p][p];
 #pragma unroll
           for (int a = p + 1; a < kMaxNg; ++a)
             if (a < Ng) {
-              const double f = M[a][p] * ip;
+              const float f = M[a][p] * ip;
 #pragma unroll
               for (int b = p + 1; b < kMaxNg; ++b)
                 if (b < Ng) M[a][b] -= f * M[p][b];
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
 #pragma unroll
       for (int a = kMaxNg - 1; a >= 0; --a)
         if (a < Ng) {
-          double v = w[a];
+          float v = w[a];
 #pragma unroll
           for (int b = a + 1; b < kMaxNg; ++b)
             if (b < Ng) v -= M[a][b] * y[b];
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
     if (tl < TB && i < ne)
 #pragma unroll
       for (int a = 0; a < kMaxNg; ++a)
-        if (a < Ng) vs[tl * Nst + a * N + k] = (float)y[a];
+        if (a < Ng) vs[tl * Nst + a * N + k] = y[a];
     __syncthreads();
     if (tl < TB && i < ne) {
       // z[a][k] = Sum_l U[k][l] y[a][l]
@@ -216,7 +217,7 @@ stdg_status visc_pc_ensure(stdg_solver* s) {
   stdg_status e = dev_alloc(s, (void**)&s->vpcU, (size_t)s->ne * NN * sizeof(float));
   if (e == STDG_OK) e = dev_alloc(s, (void**)&s->vpcLam, (size_t)s->ne * s->N * sizeof(float));
   if (e != STDG_OK) return e;
-  const size_t smem = (size_t)kEigWarps * 2 * kMaxN * kEigLd * sizeof(double);
+  const size_t smem = (size_t)kEigWarps * 2 * kMaxN * kEigLd * sizeof(float);
   STDG_CUDA(cudaFuncSetAttribute(k_visc_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int blocks = (int)std::min<int64_t>((s->ne + kEigWarps - 1) / kEigWarps, 152 * 16);
   ++s->nlaunch;
@@ -228,10 +229,10 @@ stdg_status visc_pc_ensure(stdg_solver* s) {
 // z = D^-1 r (accum: z += D^-1 r) for the viscous operator with viscosity nu.
 stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum) {
   SmallK K{};
-  for (int c = 0; c < s->Ng * s->Ng; ++c) K.v[c] = s->K[c];
+  for (int c = 0; c < s->Ng * s->Ng; ++c) K.v[c] = (float)s->K[c];
   const int N = s->N, TB = 256 / N;
   const size_t smem = (size_t)TB * N * s->Ng * sizeof(float);
-  const double c = nu * s->dt;
+  const float c = (float)(nu * s->dt);
   const int blocks = 1216;
   ++s->nlaunch;
   switch (N) {
