@@ -266,7 +266,7 @@ def main():
                     help="iteration cap per pressure solve of the plain FP64 GMRES(50) comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed_f32", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
-    ap.add_argument("--solver", default="kron_pcg", choices=["kron_cg", "kron_pcg", "kron_mg", "gmres"])
+    ap.add_argument("--solver", default="kron_mg", choices=["kron_cg", "kron_pcg", "kron_mg", "gmres"])
     ap.add_argument("--theta", type=float, default=1.0,
                     help="semi-implicit pressure weight (p_t = 0 workloads only; 1 = fully implicit)")
     ap.add_argument("--learned", action="store_true",

@@ -157,6 +157,17 @@ stdg_status stdg_reference_matrices(int p, int p_t, stdg_ref** out);
 void stdg_ref_destroy(stdg_ref* ref);
 /* K into K_host[Ng*Ng] (row a, column b). */
 stdg_status stdg_ref_time_matrix(const stdg_ref* ref, double* K_host);
+/* Real block-diagonal form of an Ng x Ng real matrix (1 <= Ng <= 5), K = W R W^-1, used to
+ * decouple the viscous systems of Eq. A1_mod in time: R has a 2 x 2 block [[a, b], [-b, a]] for
+ * every complex eigenvalue pair a +- ib (the columns of W are the real and imaginary parts of the
+ * eigenvector of a + ib) and a 1 x 1 block for every real eigenvalue; pair_host[c] = 1 marks the
+ * first column of a 2 x 2 block, 0 otherwise.  All arrays row-major, caller-owned, host memory:
+ * K_host[Ng*Ng] in; W_host, Winv_host, R_host [Ng*Ng] and pair_host[Ng] out.  STDG_EINVAL on a
+ * NULL pointer or Ng out of range; STDG_EUNSUPPORTED if the decomposition fails its own check
+ * (||K W - W R|| <= 1e-10 max(||K W||, 1), infinity-norm condition number of W <= 1e6), e.g.
+ * for a defective K.  Host-only. */
+stdg_status stdg_time_blockdiag(const double* K_host, int Ng, double* W_host, double* Winv_host,
+                                double* R_host, int* pair_host);
 /* Evaluate the reference tet basis (Sec. 2.3) at n points xi_host[n][3] of the reference
  * tetrahedron: phi_host[n][N] and reference gradients dphi_host[n][3][N] (either may be NULL).
  * Points on the edge eta + zeta = 1 or at zeta = 1 are outside the collapsed map: EINVAL. */

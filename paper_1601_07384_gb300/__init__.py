@@ -12,7 +12,7 @@ import numpy as np
 from . import _lib
 from ._lib import FIELD, PREC, SOLVER, Field, SolveStats, SolverOptions, StdgError, StepStats
 
-__all__ = ["Mesh", "Reference", "Solver", "StdgError", "beltrami", "constant", "zero", "nbasis"]
+__all__ = ["Mesh", "Reference", "Solver", "StdgError", "beltrami", "constant", "zero", "nbasis", "time_blockdiag"]
 
 
 def nbasis(p):
@@ -43,6 +43,17 @@ def constant(u):
 def zero():
     f = Field(); f.kind = FIELD["zero"]
     return f
+
+
+def time_blockdiag(K):
+    """Real block-diagonal form K = W R W^-1 (stdg_time_blockdiag): returns W, Winv, R, pair."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    n = K.shape[0]
+    W, Wi, R = np.empty((n, n)), np.empty((n, n)), np.empty((n, n))
+    pair = (C.c_int * n)()
+    _lib.check(_lib.load().stdg_time_blockdiag(K.ctypes.data_as(_lib.DP), n, W.ctypes.data_as(_lib.DP),
+                                               Wi.ctypes.data_as(_lib.DP), R.ctypes.data_as(_lib.DP), pair))
+    return W, Wi, R, np.array(pair[:], dtype=np.int64)
 
 
 class Mesh:
@@ -89,6 +100,10 @@ class Reference:
         K = np.empty((self.Ng, self.Ng))
         _lib.check(_lib.load().stdg_ref_time_matrix(self._h, K.ctypes.data_as(_lib.DP)))
         return K
+
+    def time_blockdiag(self):
+        """stdg_time_blockdiag of this reference's K: (W, Winv, R, pair) with K = W R W^-1."""
+        return time_blockdiag(self.time_matrix())
 
     def eval(self, xi):
         xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)

@@ -57,6 +57,7 @@ SIGNATURES = {
     "stdg_reference_matrices": (C.c_int, [C.c_int, C.c_int, C.POINTER(P)]),
     "stdg_ref_destroy": (None, [P]),
     "stdg_ref_time_matrix": (C.c_int, [P, DP]),
+    "stdg_time_blockdiag": (C.c_int, [DP, C.c_int, DP, DP, DP, C.POINTER(C.c_int)]),
     "stdg_ref_eval": (C.c_int, [P, DP, C.c_int64, DP, DP]),
     "stdg_tet_rule": (C.c_int, [C.c_int, DP, DP]),
     "stdg_solver_create": (C.c_int, [P, P, C.c_double, C.POINTER(SolverOptions), P, C.POINTER(P)]),

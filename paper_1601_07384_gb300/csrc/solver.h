@@ -85,6 +85,9 @@ struct stdg_solver {
   stdg::GnnState* gnn = nullptr;
   stdg::MgState* mg = nullptr;               // coarse correction of STDG_SOLVER_KRON_MG (built on first use)
   float *vpcU = nullptr, *vpcLam = nullptr;  // viscous block-Jacobi by fast diagonalisation (viscpc.cu)
+  int vbd = -1;                               // K = W R W^-1 found (1), not available (0), not tried (-1)
+  double vW[25], vWinv[25], vR[25];           // its factors (Ng x Ng, row-major)
+  int vpair[5];                               // first column of each 2 x 2 block of R
   double* kzz = nullptr;                     // FGMRES preconditioned directions
   int snap_every = 0, snap_cap = 0, nsnap = 0;
   int ah_nsnap = 0, ah_every = 0, ah_max = 0;   // harvest pairs from the pressure systems of stdg_step
@@ -165,6 +168,8 @@ void mg_free(stdg_solver* s);
 // Viscous block Jacobi (viscpc.cu): eigenvectors / eigenvalues of every tet's spatial viscous block,
 // then z = D^-1 r (accum: z += D^-1 r) with D the tet-diagonal blocks of the viscous operator.
 stdg_status visc_pc_ensure(stdg_solver* s);
-stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum);
+stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum,
+                          const double* Kt = nullptr);
+bool time_blockdiag(const double* K, int Ng, double* W, double* Winv, double* R, int* pair);
 void prof_fold(stdg_solver* s);
 }  // namespace stdg

@@ -15,6 +15,8 @@
 // needs no pivoting.
 #include <algorithm>
 #include <cmath>
+#include <complex>
+#include <vector>
 
 #include "solver.h"
 
@@ -116,9 +118,12 @@ __global__ void __launch_bounds__(32 * kEigWarps) k_visc_eig(int ne, int N, cons
 struct SmallK { float v[kMaxNg * kMaxNg]; };
 
 // z_i = D_i^-1 r_i (accum: z_i += D_i^-1 r_i), thread per (tet, spatial index), all time columns;
-// several tets per block pass with their rows staged in shared memory.  All arithmetic is binary32
-// (in binary64 the products and the divides of the small solves are FP64-pipe-bound on sm_103a);
-// the result is a fixed linear map of r, as right preconditioning requires.
+// several tets per block pass, their rows and their U staged in shared memory (U with row pitch
+// N + 1, so both the column reads of U^T r and the row reads of U y are free of bank conflicts).
+// All arithmetic is binary32 (in binary64 the products and the divides of the small solves are
+// FP64-pipe-bound on sm_103a); the result is a fixed linear map of r, as preconditioning requires.
+// K may be any Ng x Ng matrix whose symmetric part is positive semidefinite (the time matrix, or
+// its real block-diagonal form).
 template <int NC>
 __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const float* __restrict__ U,
                                                  const float* __restrict__ lam, const double* __restrict__ detJ,
@@ -126,30 +131,35 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
                                                  double* __restrict__ z, int accum) {
   extern __shared__ float vs[];
   const int N = NC ? NC : Nrt;
-  const int Nst = N * Ng;
+  const int Nst = N * Ng, NU = N * (N + 1);
   const int TB = blockDim.x / N;
   const size_t NN = (size_t)N * N;
+  float* us = vs + TB * Nst;               // TB x N x (N + 1)
   const int tl = threadIdx.x / N, k = threadIdx.x - tl * N;
   for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
+    const int nt = min(TB, ne - i0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < TB * Nst; idx += blockDim.x)
-      vs[idx] = i0 + idx / Nst < ne ? (float)r[(size_t)i0 * Nst + idx] : 0.0f;
+    for (int idx = threadIdx.x; idx < nt * Nst; idx += blockDim.x) vs[idx] = (float)r[(size_t)i0 * Nst + idx];
+    for (int idx = threadIdx.x; idx < nt * (int)NN; idx += blockDim.x) {
+      const int t = idx / (int)NN, e = idx - t * (int)NN, row = e / N;
+      us[t * NU + row * (N + 1) + (e - row * N)] = U[(size_t)i0 * NN + idx];
+    }
     __syncthreads();
     const int i = i0 + tl;
+    const bool act = tl < nt;
     float y[kMaxNg] = {0, 0, 0, 0, 0};
-    if (tl < TB && i < ne) {
+    if (act) {
       // w[a] = Sum_l U[l][k] r[a][l]
-      const float* Uc = U + (size_t)i * NN + k;
+      const float* Uc = us + tl * NU + k;
       const float* rr = vs + tl * Nst;
-      float wf[kMaxNg] = {0, 0, 0, 0, 0};
+      float w[kMaxNg] = {0, 0, 0, 0, 0};
 #pragma unroll 4
       for (int l = 0; l < N; ++l) {
-        const float u = Uc[(size_t)l * N];
+        const float u = Uc[l * (N + 1)];
 #pragma unroll
         for (int a = 0; a < kMaxNg; ++a)
-          if (a < Ng) wf[a] = fmaf(u, rr[a * N + l], wf[a]);
+          if (a < Ng) w[a] = fmaf(u, rr[a * N + l], w[a]);
       }
-      float* w = wf;
       // (d K + c lambda_k I) y = w, LU without pivoting
       const float d = (float)fabs(detJ[i]), cl = c * lam[(size_t)i * N + k];
       float M[kMaxNg][kMaxNg];
@@ -182,14 +192,14 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
         }
     }
     __syncthreads();
-    if (tl < TB && i < ne)
+    if (act)
 #pragma unroll
       for (int a = 0; a < kMaxNg; ++a)
         if (a < Ng) vs[tl * Nst + a * N + k] = y[a];
     __syncthreads();
-    if (tl < TB && i < ne) {
+    if (act) {
       // z[a][k] = Sum_l U[k][l] y[a][l]
-      const float* Ur = U + (size_t)i * NN + (size_t)k * N;
+      const float* Ur = us + tl * NU + k * (N + 1);
       const float* yy = vs + tl * Nst;
       float zz[kMaxNg] = {0, 0, 0, 0, 0};
 #pragma unroll 4
@@ -209,7 +219,255 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
   }
 }
 
+// The same with N and Ng at compile time (the solve's N, the time degree's Ng): the small solve is
+// unrolled with constant indices and U is staged by a plain contiguous copy (the tets of a pass are
+// consecutive), read by rows from its unpadded layout.
+template <int N, int NG>
+__global__ void __launch_bounds__(256) k_visc_fd_t(int ne, const float* __restrict__ U, const float* __restrict__ lam,
+                                                   const double* __restrict__ detJ, SmallK K, float c,
+                                                   const double* __restrict__ r, double* __restrict__ z, int accum) {
+  constexpr int Nst = N * NG, NN = N * N, TB = 256 / N;
+  __shared__ __align__(16) float vs[TB * Nst];
+  __shared__ __align__(16) float us[TB * NN];      // read as float4 when NN % 4 == 0
+  const int tl = threadIdx.x / N, k = threadIdx.x - tl * N;
+  float Kc[NG][NG];
+#pragma unroll
+  for (int a = 0; a < NG; ++a)
+#pragma unroll
+    for (int b = 0; b < NG; ++b) Kc[a][b] = K.v[a * NG + b];
+  for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
+    const int nt = min(TB, ne - i0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nt * Nst; idx += blockDim.x) vs[idx] = (float)r[(size_t)i0 * Nst + idx];
+    const float* Ug = U + (size_t)i0 * NN;
+    if (NN % 4 == 0) {
+      const float4* U4 = reinterpret_cast<const float4*>(Ug);
+      float4* u4 = reinterpret_cast<float4*>(us);
+      for (int idx = threadIdx.x; idx < nt * NN / 4; idx += blockDim.x) u4[idx] = U4[idx];
+    } else {
+      for (int idx = threadIdx.x; idx < nt * NN; idx += blockDim.x) us[idx] = Ug[idx];
+    }
+    __syncthreads();
+    const int i = i0 + tl;
+    const bool act = tl < nt;
+    float y[NG];
+    if (act) {
+      const float* Uc = us + tl * NN + k;
+      const float* rr = vs + tl * Nst;
+      float w[NG];
+#pragma unroll
+      for (int a = 0; a < NG; ++a) w[a] = 0.0f;
+#pragma unroll 5
+      for (int l = 0; l < N; ++l) {
+        const float u = Uc[l * N];
+#pragma unroll
+        for (int a = 0; a < NG; ++a) w[a] = fmaf(u, rr[a * N + l], w[a]);
+      }
+      const float d = (float)detJ[i], cl = c * lam[(size_t)i * N + k];
+      float M[NG][NG];
+#pragma unroll
+      for (int a = 0; a < NG; ++a)
+#pragma unroll
+        for (int b = 0; b < NG; ++b) M[a][b] = d * Kc[a][b] + (a == b ? cl : 0.0f);
+#pragma unroll
+      for (int p = 0; p < NG; ++p) {
+        const float ip = 1.0f / M[p][p];
+#pragma unroll
+        for (int a = p + 1; a < NG; ++a) {
+          const float f = M[a][p] * ip;
+#pragma unroll
+          for (int b = p + 1; b < NG; ++b) M[a][b] -= f * M[p][b];
+          w[a] -= f * w[p];
+        }
+      }
+#pragma unroll
+      for (int a = NG - 1; a >= 0; --a) {
+        float v = w[a];
+#pragma unroll
+        for (int b = a + 1; b < NG; ++b) v -= M[a][b] * y[b];
+        y[a] = v / M[a][a];
+      }
+    }
+    __syncthreads();
+    if (act)
+#pragma unroll
+      for (int a = 0; a < NG; ++a) vs[tl * Nst + a * N + k] = y[a];
+    __syncthreads();
+    if (act) {
+      const float* Ur = us + tl * NN + k * N;
+      const float* yy = vs + tl * Nst;
+      float zz[NG];
+#pragma unroll
+      for (int a = 0; a < NG; ++a) zz[a] = 0.0f;
+#pragma unroll 5
+      for (int l = 0; l < N; ++l) {
+        const float u = Ur[l];
+#pragma unroll
+        for (int a = 0; a < NG; ++a) zz[a] = fmaf(u, yy[a * N + l], zz[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NG; ++a) {
+        const size_t o = (size_t)i * Nst + a * N + k;
+        z[o] = accum ? z[o] + (double)zz[a] : (double)zz[a];
+      }
+    }
+  }
+}
+
+template <int N>
+static void launch_fd_t(int Ng, int blocks, cudaStream_t st, int ne, const float* U, const float* lam,
+                        const double* detJ, const SmallK& K, float c, const double* r, double* z, int accum) {
+  switch (Ng) {
+    case 1: k_visc_fd_t<N, 1><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 2: k_visc_fd_t<N, 2><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 3: k_visc_fd_t<N, 3><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 4: k_visc_fd_t<N, 4><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    default: k_visc_fd_t<N, 5><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+  }
+}
+
 }  // namespace
+
+// Real block-diagonal form of the time matrix, K = W R W^-1: R has a 2 x 2 block [[a, b], [-b, a]]
+// for every complex eigenvalue pair a +- ib (columns vr, vi of W: the real and imaginary parts of
+// the eigenvector of a + ib) and a 1 x 1 block for every real eigenvalue.  pair[c] = 1 marks the
+// first column of a 2 x 2 block.  Eigenvalues from the characteristic polynomial (Faddeev-LeVerrier
+// coefficients, Durand-Kerner iteration), eigenvectors by complex elimination; the result is checked
+// (||K W - W R||, cond(W) <= 1e6) and false is returned if it fails.  Ng <= 5.
+bool time_blockdiag(const double* K, int Ng, double* W, double* Winv, double* R, int* pair) {
+  using cd = std::complex<double>;
+  const int n = Ng;
+  // characteristic polynomial det(lambda I - K) = lambda^n + c[1] lambda^(n-1) + ... + c[n]
+  std::vector<double> c(n + 1, 0.0), M(n * n, 0.0), KM(n * n);
+  c[0] = 1.0;
+  for (int k = 1; k <= n; ++k) {
+    // M_k = K M_{k-1} + c_{k-1} I,  c_k = -tr(K M_k) / k
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double v = 0.0;
+        for (int l = 0; l < n; ++l) v += K[i * n + l] * M[l * n + j];
+        KM[i * n + j] = v;
+      }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) M[i * n + j] = KM[i * n + j] + (i == j ? c[k - 1] : 0.0);
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int l = 0; l < n; ++l) tr += K[i * n + l] * M[l * n + i];
+    c[k] = -tr / k;
+  }
+  auto poly = [&](cd z) { cd v = 1.0; for (int k = 1; k <= n; ++k) v = v * z + c[k]; return v; };
+  double rad = 1.0;
+  for (int k = 1; k <= n; ++k) rad = std::max(rad, 1.0 + std::fabs(c[k]));
+  std::vector<cd> z(n);
+  for (int k = 0; k < n; ++k) z[k] = std::polar(0.5 * rad, 0.4 + 6.283185307179586 * k / n);
+  for (int it = 0; it < 500; ++it) {
+    double moved = 0.0;
+    for (int k = 0; k < n; ++k) {
+      cd den = 1.0;
+      for (int j = 0; j < n; ++j) if (j != k) den *= (z[k] - z[j]);
+      if (std::abs(den) == 0.0) return false;
+      const cd d = poly(z[k]) / den;
+      z[k] -= d;
+      moved = std::max(moved, std::abs(d) / std::max(1.0, std::abs(z[k])));
+    }
+    if (moved < 1e-15) break;
+  }
+  // pair up: real roots, then one representative (imaginary part > 0) per conjugate pair
+  std::vector<cd> reps;
+  std::vector<int> used(n, 0);
+  const double tiny = 1e-9 * rad;
+  for (int k = 0; k < n; ++k)
+    if (std::fabs(z[k].imag()) <= tiny) reps.push_back(cd(z[k].real(), 0.0)), used[k] = 1;
+  for (int k = 0; k < n; ++k)
+    if (!used[k] && z[k].imag() > 0.0) reps.push_back(z[k]);
+  int cols = 0;
+  for (const cd& l : reps) cols += l.imag() == 0.0 ? 1 : 2;
+  if (cols != n) return false;
+  std::vector<double> Wm(n * n, 0.0), Rm(n * n, 0.0);
+  int col = 0;
+  for (const cd& l : reps) {
+    // null vector of (K - l I): Gaussian elimination with full pivoting, last free variable = 1
+    std::vector<cd> A(n * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i * n + j] = cd(K[i * n + j]) - (i == j ? l : cd(0.0));
+    std::vector<int> perm(n);
+    for (int j = 0; j < n; ++j) perm[j] = j;
+    for (int k = 0; k < n - 1; ++k) {
+      int pi = k, pj = k;
+      for (int i = k; i < n; ++i)
+        for (int j = k; j < n; ++j)
+          if (std::abs(A[i * n + j]) > std::abs(A[pi * n + pj])) pi = i, pj = j;
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[pi * n + j]);
+      for (int i = 0; i < n; ++i) std::swap(A[i * n + k], A[i * n + pj]);
+      std::swap(perm[k], perm[pj]);
+      if (std::abs(A[k * n + k]) == 0.0) return false;
+      for (int i = k + 1; i < n; ++i) {
+        const cd f = A[i * n + k] / A[k * n + k];
+        for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      }
+    }
+    std::vector<cd> y(n);
+    y[n - 1] = 1.0;
+    for (int k = n - 2; k >= 0; --k) {
+      cd v = 0.0;
+      for (int j = k + 1; j < n; ++j) v -= A[k * n + j] * y[j];
+      y[k] = v / A[k * n + k];
+    }
+    std::vector<cd> v(n);
+    for (int j = 0; j < n; ++j) v[perm[j]] = y[j];
+    double nrm = 0.0;
+    for (const cd& e : v) nrm += std::norm(e);
+    nrm = std::sqrt(nrm);
+    for (cd& e : v) e /= nrm;
+    if (l.imag() == 0.0) {
+      for (int i = 0; i < n; ++i) Wm[i * n + col] = v[i].real();
+      Rm[col * n + col] = l.real();
+      pair[col] = 0;
+      ++col;
+    } else {
+      for (int i = 0; i < n; ++i) { Wm[i * n + col] = v[i].real(); Wm[i * n + col + 1] = v[i].imag(); }
+      Rm[col * n + col] = l.real();       Rm[col * n + col + 1] = l.imag();
+      Rm[(col + 1) * n + col] = -l.imag(); Rm[(col + 1) * n + col + 1] = l.real();
+      pair[col] = 1; pair[col + 1] = 0;
+      col += 2;
+    }
+  }
+  // W^-1 by Gauss-Jordan with partial pivoting
+  std::vector<double> A(Wm), I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int pi = k;
+    for (int i = k + 1; i < n; ++i) if (std::fabs(A[i * n + k]) > std::fabs(A[pi * n + k])) pi = i;
+    if (std::fabs(A[pi * n + k]) < 1e-12) return false;
+    for (int j = 0; j < n; ++j) { std::swap(A[k * n + j], A[pi * n + j]); std::swap(I[k * n + j], I[pi * n + j]); }
+    const double d = A[k * n + k];
+    for (int j = 0; j < n; ++j) { A[k * n + j] /= d; I[k * n + j] /= d; }
+    for (int i = 0; i < n; ++i)
+      if (i != k) {
+        const double f = A[i * n + k];
+        for (int j = 0; j < n; ++j) { A[i * n + j] -= f * A[k * n + j]; I[i * n + j] -= f * I[k * n + j]; }
+      }
+  }
+  // check K W = W R
+  double err = 0.0, ref = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double kw = 0.0, wr = 0.0;
+      for (int l = 0; l < n; ++l) { kw += K[i * n + l] * Wm[l * n + j]; wr += Wm[i * n + l] * Rm[l * n + j]; }
+      err = std::max(err, std::fabs(kw - wr));
+      ref = std::max(ref, std::fabs(kw));
+    }
+  if (!(err <= 1e-10 * std::max(ref, 1.0))) return false;
+  double nw = 0.0, ni = 0.0;                      // infinity-norm condition number of W
+  for (int i = 0; i < n; ++i) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < n; ++j) { a += std::fabs(Wm[i * n + j]); b += std::fabs(I[i * n + j]); }
+    nw = std::max(nw, a); ni = std::max(ni, b);
+  }
+  if (!(nw * ni <= 1e6)) return false;
+  for (int q = 0; q < n * n; ++q) { W[q] = Wm[q]; Winv[q] = I[q]; R[q] = Rm[q]; }
+  return true;
+}
 
 stdg_status visc_pc_ensure(stdg_solver* s) {
   if (s->vpcU) return STDG_OK;
@@ -226,19 +484,20 @@ stdg_status visc_pc_ensure(stdg_solver* s) {
   return STDG_OK;
 }
 
-// z = D^-1 r (accum: z += D^-1 r) for the viscous operator with viscosity nu.
-stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum) {
+// z = D^-1 r (accum: z += D^-1 r) for the viscous operator with viscosity nu; with Kt, for the
+// operator whose time matrix is Kt instead of K (the block-diagonal form of the decoupled solve).
+stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum, const double* Kt) {
   SmallK K{};
-  for (int c = 0; c < s->Ng * s->Ng; ++c) K.v[c] = (float)s->K[c];
+  for (int c = 0; c < s->Ng * s->Ng; ++c) K.v[c] = (float)(Kt ? Kt[c] : s->K[c]);
   const int N = s->N, TB = 256 / N;
-  const size_t smem = (size_t)TB * N * s->Ng * sizeof(float);
+  const size_t smem = ((size_t)TB * N * s->Ng + (size_t)TB * N * (N + 1)) * sizeof(float);
   const float c = (float)(nu * s->dt);
   const int blocks = 1216;
   ++s->nlaunch;
   switch (N) {
-    case 20: k_visc_fd<20><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
-    case 35: k_visc_fd<35><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
-    case 10: k_visc_fd<10><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
+    case 20: launch_fd_t<20>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
+    case 35: launch_fd_t<35>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
+    case 10: launch_fd_t<10>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
     default: k_visc_fd<0><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
   }
   STDG_LAUNCH_CHECK();
@@ -246,3 +505,15 @@ stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z,
 }
 
 }  // namespace stdg
+
+extern "C" stdg_status stdg_time_blockdiag(const double* K, int Ng, double* W, double* Winv, double* R, int* pair) {
+  if (!K || !W || !Winv || !R || !pair || Ng < 1 || Ng > stdg::kMaxNg) {
+    stdg::set_error("stdg_time_blockdiag: NULL argument or Ng outside 1..%d", stdg::kMaxNg);
+    return STDG_EINVAL;
+  }
+  if (!stdg::time_blockdiag(K, Ng, W, Winv, R, pair)) {
+    stdg::set_error("stdg_time_blockdiag: no well-conditioned real block-diagonal form");
+    return STDG_EUNSUPPORTED;
+  }
+  return STDG_OK;
+}

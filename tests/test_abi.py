@@ -90,3 +90,48 @@ def test_time_matrix_matches_oracle(lib, pt):
     d = SpaceTimeDG(Mesh(v, t), 1, pt, 0.1)
     Kor = d.face_blocks(0)["M"][::d.N, ::d.N]
     assert np.abs(g.Reference(1, pt).time_matrix() - Kor).max() < 1e-13
+
+
+@pytest.mark.parametrize("pt", [0, 1, 2, 3, 4])
+def test_time_blockdiag_of_the_time_matrix(lib, pt):
+    """stdg_time_blockdiag (host logic of the time-decoupled viscous solve): K = W R W^-1 with R real
+    block diagonal, whose blocks carry exactly the eigenvalues numpy finds for K."""
+    import paper_1601_07384_gb300 as g
+    K = g.Reference(1, pt).time_matrix()
+    W, Wi, R, pair = g.time_blockdiag(K)
+    n = pt + 1
+    assert np.abs(K @ W - W @ R).max() <= 1e-12 * max(1.0, np.abs(K).max())
+    assert np.abs(W @ Wi - np.eye(n)).max() <= 1e-12
+    ev = []
+    mask = np.zeros((n, n), dtype=bool)
+    a = 0
+    while a < n:
+        if pair[a]:
+            assert R[a, a] == R[a + 1, a + 1] and R[a, a + 1] == -R[a + 1, a] and R[a, a + 1] != 0
+            ev += [complex(R[a, a], R[a, a + 1]), complex(R[a, a], -R[a, a + 1])]
+            mask[a:a + 2, a:a + 2] = True
+            a += 2
+        else:
+            ev.append(complex(R[a, a], 0.0))
+            mask[a, a] = True
+            a += 1
+    assert np.all(R[~mask] == 0.0)
+    ref = np.linalg.eigvals(K)
+    key = lambda z: (round(z.real, 9), round(z.imag, 9))
+    assert np.allclose(sorted(ev, key=key), sorted(ref, key=key), atol=1e-10)
+    # K + K^T is positive semidefinite, so every eigenvalue has a nonnegative real part
+    assert min(z.real for z in ev) >= -1e-12
+
+
+def test_time_blockdiag_rotation_and_errors(lib):
+    """A scaled rotation is its own block-diagonal form; bad arguments are rejected."""
+    import paper_1601_07384_gb300 as g
+    th = 0.7
+    K = 2.0 * np.array([[np.cos(th), np.sin(th), 0.0], [-np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 0.5]])
+    P = np.array([[1.0, 2.0, 0.0], [0.0, 1.0, 1.0], [1.0, 0.0, 3.0]])
+    W, Wi, R, pair = g.time_blockdiag(P @ K @ np.linalg.inv(P))
+    assert sorted(np.round(np.linalg.eigvals(R), 10), key=lambda z: (z.real, z.imag)) == \
+        sorted(np.round(np.linalg.eigvals(K), 10), key=lambda z: (z.real, z.imag))
+    assert int(pair.sum()) == 1
+    with pytest.raises(g.StdgError):
+        g.time_blockdiag(np.eye(6))
