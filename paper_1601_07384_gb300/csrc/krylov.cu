@@ -1458,17 +1458,34 @@ __global__ void k_final_norm(int nparts, const double* __restrict__ part, double
   }
 }
 
-// COCG on the decoupled viscous systems; x holds the initial guess and receives the solution.
-// Returns STDG_EUNSUPPORTED when K has no usable block-diagonal form (the caller then uses GMRES),
-// STDG_ENOCONV / STDG_ENAN as the other solvers.
+__global__ void k_f64_from_f32(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (double)in[e];
+}
+__global__ void k_add(int64_t n, const double* __restrict__ d, double* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += d[e];
+}
+
+// COCG on the decoupled viscous systems; x holds the initial guess (zero_x0: x = 0) and receives the
+// solution.  lowprec: the operator is applied with binary32 blocks (vectors converted around the
+// launch), for the inner solves of the refinement in solve_viscous.  Returns STDG_EUNSUPPORTED when
+// K has no usable block-diagonal form (the caller then uses GMRES), STDG_ENOCONV / STDG_ENAN as the
+// other solvers.
 static stdg_status cocg_viscous(stdg_solver* s, const ApplyArgs& a, double nu, const double* b, double* x,
-                                double tol_abs, int* iters, double* res) {
+                                double tol_abs, int* iters, double* res, bool zero_x0 = false,
+                                bool lowprec = false) {
   const int Ng = s->Ng, N = s->N;
   const int64_t n = s->ne * (int64_t)s->Nst;
   if (s->vbd < 0) s->vbd = time_blockdiag(s->K.data(), Ng, s->vW, s->vWinv, s->vR, s->vpair) ? 1 : 0;
   if (!s->vbd) return STDG_EUNSUPPORTED;
   stdg_status e = visc_pc_ensure(s);
+  if (e == STDG_OK && lowprec) e = ensure_lowprec(s);
   if (e != STDG_OK) return e;
+  if (lowprec) {
+    cudaError_t ce = warp_prepare_f32_visc(s);
+    if (ce != cudaSuccess) { set_error("binary32 viscous blocks: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  }
   TpArg W{}, Wi{};
   PairArg pr{};
   for (int q = 0; q < Ng * Ng; ++q) { W.v[q] = s->vW[q]; Wi.v[q] = s->vWinv[q]; }
@@ -1482,12 +1499,28 @@ static stdg_status cocg_viscous(stdg_solver* s, const ApplyArgs& a, double nu, c
   double* Ma = s->scal + 340; double* Mb = s->scal + 370;   // Ng^2 each
   double* flag = s->scal + 398; double* resd = s->scal + 399;
   const int G2 = Ng * Ng;
-  s->nlaunch += 2;
-  k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Wi, 1.0, x, y);
+  const LpKernels lk = lp_kernels();
+  auto apply = [&](const double* in, double* out) -> stdg_status {
+    if (!lowprec) return op_apply(s, at, in, out);
+    lk.f32(s->stream, n, in, s->fp);
+    const cudaError_t ce = warp_launch_f32_visc(s, s->fp, s->fq, at.scale, at.mass_coef, at.Kmass);
+    if (ce != cudaSuccess) { set_error("binary32 viscous operator: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+    k_f64_from_f32<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, s->fq, out);
+    s->nlaunch += 3;
+    ++s->op_launches;
+    return STDG_OK;
+  };
+  s->nlaunch += 1;
   k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Wi, 1.0, b, bt);
-  if ((e = op_apply(s, at, y, r)) != STDG_OK) return e;
-  ++s->nlaunch;
-  k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, bt, nullptr, 1, r);
+  if (zero_x0) {
+    cudaMemsetAsync(y, 0, n * sizeof(double), s->stream);
+    cudaMemcpyAsync(r, bt, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  } else {
+    s->nlaunch += 2;
+    k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Wi, 1.0, x, y);
+    if ((e = apply(y, r)) != STDG_OK) return e;
+    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, bt, nullptr, 1, r);
+  }
   if ((e = visc_pc_apply(s, nu, r, z, 0, s->vR)) != STDG_OK) return e;
   cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   cudaMemsetAsync(flag, 0, sizeof(double), s->stream);
@@ -1501,7 +1534,7 @@ static stdg_status cocg_viscous(stdg_solver* s, const ApplyArgs& a, double nu, c
   const int B = s->opt.graph_batch > 1 ? std::min(4, s->opt.graph_batch) : 1;
   auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
     if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
-    stdg_status e2 = op_apply(s, at, p, q);
+    stdg_status e2 = apply(p, q);
     if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
     if (e2 != STDG_OK) return e2;
     const int want = slot == B - 1;
@@ -1522,14 +1555,15 @@ static stdg_status cocg_viscous(stdg_solver* s, const ApplyArgs& a, double nu, c
   };
   int it = 0;
   double rabs = INFINITY;
-  const int kind = df_serves(s, at) ? 1 : 0;
+  const int kind = lowprec ? 2 : df_serves(s, at) ? 1 : 0;
+  const int kpi = 11 + (lowprec ? 2 : 0);
   if (B > 1) {
-    e = run_batched(s, B, 11, s->opt.max_iters, tol_abs, body, &it, &rabs, kind, true);
+    e = run_batched(s, B, kpi, s->opt.max_iters, tol_abs, body, &it, &rabs, kind, true);
   } else {
     e = STDG_OK;
     while (it < s->opt.max_iters) {
       if ((e = body(0, nullptr)) != STDG_OK) break;
-      s->nlaunch += 11;
+      s->nlaunch += kpi;
       ++it;
       if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("viscous COCG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
       rabs = s->hostbuf[0];
@@ -1577,6 +1611,32 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
     return cg_block(s, a, b, x, false, I, tol * bn, iters, res);
   }
   int it1 = 0;
+  if (use_cocg && s->opt.precision == STDG_PREC_MIXED_F32 && s->vbd != 0) {
+    // mixed precision: binary64 refinement around binary32 inner COCG solves.  Each outer step forms
+    // the true residual r = b - A x with the binary64-accurate operator and solves A d = r with the
+    // binary32 operator to 1e-5 ||r|| (its rounding limits how far an inner solve can go), x += d.
+    stdg_status e0 = ensure_basis(s, 2);
+    if (e0 != STDG_OK) return e0;
+    double* ro = s->basis;
+    double* d = s->basis + (size_t)s->ne * s->Nst;
+    const int64_t nn = s->ne * (int64_t)s->Nst;
+    for (int outer = 0; outer < 8; ++outer) {
+      if ((e0 = op_apply(s, a, x, ro)) != STDG_OK) return e0;
+      ++s->nlaunch;
+      k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(nn, b, nullptr, 1, ro);
+      const double nr = host_norm(s, ro, nn);
+      if (!std::isfinite(nr)) { set_error("viscous solve: non-finite residual"); return STDG_ENAN; }
+      if (nr <= tol * bn) { *iters = it1; *res = nr; return STDG_OK; }
+      int itk = 0;
+      double rk = 0.0;
+      e0 = cocg_viscous(s, a, nu, ro, d, std::max(1e-5 * nr, 0.5 * tol * bn), &itk, &rk, true, true);
+      it1 += itk;
+      if (e0 == STDG_EUNSUPPORTED || e0 == STDG_ENOCONV) break;   // binary64 solvers below
+      if (e0 != STDG_OK) return e0;
+      ++s->nlaunch;
+      k_add<<<kRedBlocks, kRedThreads, 0, s->stream>>>(nn, d, x);
+    }
+  }
   if (use_cocg) {
     double r1 = 0.0;
     // half the tolerance: the recursively updated residual may drift from the true one by rounding

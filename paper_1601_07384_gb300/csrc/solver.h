@@ -52,6 +52,7 @@ struct stdg_solver {
   void *wB = nullptr, *wA = nullptr;          // warp-kernel block copies (binary32 / bfloat16), padded rows
   void *wdB = nullptr, *wdA = nullptr;        // warp-kernel (hi, lo) binary32 planes of the FP64 blocks
   void *wdBv = nullptr;                       // same for the viscous diagonal blocks B_i - Bvisc_i
+  void *wBv32 = nullptr;                      // the viscous diagonal blocks in binary32 (padded rows)
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
@@ -138,6 +139,9 @@ int warp_df_warps_per_sm(stdg_solver* s);                  // resident warps per
 cudaError_t launch_apply_warp_lp(stdg_solver* s, const float* x, float* y, int pinned, int kron, float scale,
                                  float pin_diag, double* dotpart = nullptr);
 int warp_blocks_lp(stdg_solver* s);   // blocks of the binary32 operator launch (dot partials it writes)
+cudaError_t warp_prepare_f32_visc(stdg_solver* s);        // binary32 viscous operator (mixed_f32 only)
+cudaError_t warp_launch_f32_visc(stdg_solver* s, const float* x, float* y, double scale, double mass_coef,
+                                 const double* Kmass);
 cudaError_t launch_apply_warp_df(stdg_solver* s, const double* x, double* y, int pinned, int kron, double scale,
                                  double pin_diag);
 cudaError_t launch_apply_warp_df_visc(stdg_solver* s, const double* x, double* y, double scale, double mass_coef,
