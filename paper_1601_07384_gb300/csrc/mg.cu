@@ -70,6 +70,11 @@ __device__ inline void mg_block_store(double* v, int cnt, double* part) {
   }
 }
 
+__device__ inline float mg_warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Fine residual's constant modes -> level 1: for every level-1 cell, the sum over its tets of the
 // residual after one damped Jacobi sweep from zero, s_i = r_i - Sum_j S0_ij (omega / S0_jj) r_j.
 // The pinned coefficient (tet 0) is read as 0.
@@ -78,24 +83,28 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_down0(int nc, int Ng, int N, 
                                                          const int* __restrict__ cidx, const int* __restrict__ t2n,
                                                          const float* __restrict__ a0, const float* __restrict__ d0,
                                                          const T* __restrict__ r, float* __restrict__ rc) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+  // one warp per level-1 cell; lane t handles term t % 5 (diagonal or face t % 5 - 1) of child t / 5
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nc; c += gridDim.x * wpb) {
     float acc[kMaxNg] = {0, 0, 0, 0, 0};
-    for (int k = cptr[c]; k < cptr[c + 1]; ++k) {
-      const int i = cidx[k];
+    const int k0 = cptr[c], nk = cptr[c + 1] - k0;
+    for (int t = lane; t < 5 * nk; t += 32) {
+      const int i = cidx[k0 + t / 5], f = t % 5;
       if (i == 0) continue;                        // pinned: contributes nothing
       const float* a = a0 + (size_t)i * 5;
-      const float wi = a[0] * d0[i];
+      if (f == 0) {
+        const float wi = a[0] * d0[i];
 #pragma unroll
-      for (int q = 0; q < kMaxNg; ++q)
-        if (q < Ng) {
-          const float ri = (float)r[(size_t)i * Nst + q * N];
-          acc[q] += ri - wi * ri;
-        }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int nb = t2n[4 * i + f];
+        for (int q = 0; q < kMaxNg; ++q)
+          if (q < Ng) {
+            const float ri = (float)r[(size_t)i * Nst + q * N];
+            acc[q] += ri - wi * ri;
+          }
+      } else {
+        const int nb = t2n[4 * i + f - 1];
         if (nb <= 0) continue;                     // boundary, or the pinned tet (coefficient 0)
-        const float w = a[1 + f] * d0[nb];
+        const float w = a[f] * d0[nb];
 #pragma unroll
         for (int q = 0; q < kMaxNg; ++q)
           if (q < Ng) acc[q] -= w * (float)r[(size_t)nb * Nst + q * N];
@@ -103,24 +112,31 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_down0(int nc, int Ng, int N, 
     }
 #pragma unroll
     for (int q = 0; q < kMaxNg; ++q)
-      if (q < Ng) rc[(size_t)c * Ng + q] = acc[q];
+      if (q < Ng) {
+        const float v = mg_warp_sum(acc[q]);
+        if (lane == 0) rc[(size_t)c * Ng + q] = v;
+      }
   }
 }
 
-// Level l -> l+1: the same on a CSR level.
+// Level l -> l+1: the same on a CSR level; one warp per coarse cell, lane (child slot t / 4, every
+// fourth entry of that child's row from t % 4).
 __global__ void __launch_bounds__(kMgThreads) k_mg_down(int nc, int Ng, const int* __restrict__ cptr,
                                                         const int* __restrict__ cidx, const int* __restrict__ rp,
                                                         const int* __restrict__ ci, const float* __restrict__ va,
                                                         const float* __restrict__ dl, const float* __restrict__ r,
                                                         float* __restrict__ rc) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, slot = lane >> 2, sub = lane & 3;
+  const int wpb = blockDim.x >> 5;
+  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nc; c += gridDim.x * wpb) {
     float acc[kMaxNg] = {0, 0, 0, 0, 0};
-    for (int k = cptr[c]; k < cptr[c + 1]; ++k) {
+    for (int k = cptr[c] + slot; k < cptr[c + 1]; k += 8) {
       const int i = cidx[k];
+      if (sub == 0)
 #pragma unroll
-      for (int q = 0; q < kMaxNg; ++q)
-        if (q < Ng) acc[q] += r[(size_t)i * Ng + q];
-      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        for (int q = 0; q < kMaxNg; ++q)
+          if (q < Ng) acc[q] += r[(size_t)i * Ng + q];
+      for (int e = rp[i] + sub; e < rp[i + 1]; e += 4) {
         const int j = ci[e];
         const float w = va[e] * dl[j];
 #pragma unroll
@@ -130,27 +146,35 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_down(int nc, int Ng, const in
     }
 #pragma unroll
     for (int q = 0; q < kMaxNg; ++q)
-      if (q < Ng) rc[(size_t)c * Ng + q] = acc[q];
+      if (q < Ng) {
+        const float v = mg_warp_sum(acc[q]);
+        if (lane == 0) rc[(size_t)c * Ng + q] = v;
+      }
   }
 }
 
-// Coarsest level: x = C^-1 r with the dense symmetric inverse (column j read as row j).
+// Coarsest level: x = C^-1 r with the dense symmetric inverse, one warp per row (row i of the
+// inverse read contiguously), r staged in shared memory by every block.
 __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(int n, int Ng, const float* __restrict__ cinv,
                                                           const float* __restrict__ r, float* __restrict__ x) {
   __shared__ float rs[kCoarseMax * kMaxNg];
   for (int k = threadIdx.x; k < n * Ng; k += blockDim.x) rs[k] = r[k];
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
     float acc[kMaxNg] = {0, 0, 0, 0, 0};
-    for (int j = 0; j < n; ++j) {
-      const float c = cinv[(size_t)j * n + i];
+    for (int j = lane; j < n; j += 32) {
+      const float c = cinv[(size_t)i * n + j];
 #pragma unroll
       for (int q = 0; q < kMaxNg; ++q)
         if (q < Ng) acc[q] = fmaf(c, rs[j * Ng + q], acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < kMaxNg; ++q)
-      if (q < Ng) x[(size_t)i * Ng + q] = acc[q];
+      if (q < Ng) {
+        const float v = mg_warp_sum(acc[q]);
+        if (lane == 0) x[(size_t)i * Ng + q] = v;
+      }
   }
 }
 
@@ -231,6 +255,8 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_up0(int ne, int Ng, int N, in
 }
 
 inline int mg_grid(int n) { return std::max(1, std::min((n + kMgThreads - 1) / kMgThreads, 1216)); }
+// grid for one warp per item
+inline int mg_wgrid(int n) { return std::max(1, std::min((n + kMgThreads / 32 - 1) / (kMgThreads / 32), 4864)); }
 
 // Galerkin product of a CSR level with piecewise-constant prolongation (cell c of the finer level
 // -> agg[c]), summed in binary64.
@@ -472,12 +498,12 @@ static void mg_apply_t(stdg_solver* s, const T* r, T* z, double* part) {
   const int Ng = s->Ng, N = s->N, Nst = s->Nst, L = mg->L, ne = (int)s->ne;
   cudaStream_t st = s->stream;
   MgLevel* lv = mg->lv;
-  k_mg_down0<T><<<mg_grid(lv[1].n), kMgThreads, 0, st>>>(lv[1].n, Ng, N, Nst, lv[1].cptr, lv[1].cidx, s->dm.t2n,
+  k_mg_down0<T><<<mg_wgrid(lv[1].n), kMgThreads, 0, st>>>(lv[1].n, Ng, N, Nst, lv[1].cptr, lv[1].cidx, s->dm.t2n,
                                                           mg->a0, mg->d0, r, lv[1].r);
   for (int l = 1; l < L; ++l)
-    k_mg_down<<<mg_grid(lv[l + 1].n), kMgThreads, 0, st>>>(lv[l + 1].n, Ng, lv[l + 1].cptr, lv[l + 1].cidx, lv[l].rp,
+    k_mg_down<<<mg_wgrid(lv[l + 1].n), kMgThreads, 0, st>>>(lv[l + 1].n, Ng, lv[l + 1].cptr, lv[l + 1].cidx, lv[l].rp,
                                                            lv[l].ci, lv[l].va, lv[l].dl, lv[l].r, lv[l + 1].r);
-  k_mg_coarse<<<mg_grid(lv[L].n), kMgThreads, 0, st>>>(lv[L].n, Ng, mg->cinv, lv[L].r, lv[L].x);
+  k_mg_coarse<<<mg_wgrid(lv[L].n), kMgThreads, 0, st>>>(lv[L].n, Ng, mg->cinv, lv[L].r, lv[L].x);
   for (int l = L - 1; l >= 1; --l)
     k_mg_up<<<mg_grid(lv[l].n), kMgThreads, 0, st>>>(lv[l].n, Ng, lv[l].rp, lv[l].ci, lv[l].va, lv[l].dl, lv[l].par,
                                                      lv[l].r, lv[l + 1].x, lv[l].x);
