@@ -82,6 +82,7 @@ struct stdg_solver {
   double *fac_x = nullptr, *fac_v = nullptr;   // factored-form cross-check operator (lazily allocated)
   double theta = 1.0;                          // semi-implicit pressure weight (p_t = 0 only)
   double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
+  float2 *cphiP = nullptr, *cdphiP = nullptr, *cfphiP = nullptr;   // convection tables as (hi, lo) pairs
   std::vector<void*> allocs;
   stdg::GnnState* gnn = nullptr;
   stdg::MgState* mg = nullptr;               // coarse correction of STDG_SOLVER_KRON_MG (built on first use)

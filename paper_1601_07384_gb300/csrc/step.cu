@@ -305,22 +305,55 @@ struct ConvArgs {
 // evaluated at the n_t time points from them, and the time test functions are folded in at once,
 // G[q][c][e][a] = Sum_t gamma_a(tau_t) H(x_q, tau_t)[c][e]; the spatial test functions are applied
 // in a second pass.  Compared with evaluating every space-time point from scratch this divides the
-// binary64 work by n_t (3 at p_t = 1, 7 at p_t = 4); the sums are the same up to rounding order.
+// work by n_t (3 at p_t = 1, 7 at p_t = 4); the sums are the same up to rounding order.
+//
+// The two dense contractions (basis values x coefficients, and test functions x G) are formed from
+// binary32 pairs, a = hi + lo with hi = fl32(a), lo = fl32(a - hi): each product hi_a hi_b is exact by
+// an FMA, the cross terms are added to its error, and the sum is kept as an unevaluated binary32
+// pair (TwoSum), converted to binary64 at the end of the sum.  That is binary64-accurate (relative
+// error ~1e-14 of the sum of |terms|) at 12 FP32 operations per term on a pipe 64 times faster than
+// sm_103a's FP64 pipe, which the binary64 kernel kept 86 % busy.  The flux itself (products of the
+// velocities, the Rusanov speed) stays binary64.
 constexpr int kConvCH = 128;        // spatial points per pass (= threads per block)
-__global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
+
+__device__ __forceinline__ float2 pair_split(double a) {
+  const float h = (float)a;
+  return make_float2(h, (float)(a - (double)h));
+}
+// (s, c) += a b for pairs a, b: TwoProd of the high parts, cross terms into the error, TwoSum into s
+__device__ __forceinline__ void pair_fma(float2 a, float2 b, float& s, float& c) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p);
+  const float t = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+  const float s2 = s + p;
+  const float bb = s2 - s;
+  c += ((s - (s2 - bb)) + (p - bb)) + t;
+  s = s2;
+}
+__device__ __forceinline__ double pair_value(float s, float c) { return (double)s + (double)c; }
+
+__global__ void k_split_pairs(int64_t n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = pair_split(in[e]);
+}
+
+__global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2* __restrict__ phiP,
+                                                        const float2* __restrict__ dphiP,
+                                                        const float2* __restrict__ fphiP) {
   extern __shared__ double sm[];
   const int i = blockIdx.x, N = a.N, Ng = a.Ng, Nst = N * Ng, ne = a.ne, nt = a.nt;
-  double* acc = sm;                      // 3 x Nst
-  double* Vi = acc + 3 * Nst;            // 3 x Nst (own coefficients)
-  double* Vn = Vi + 3 * Nst;             // 3 x Nst (neighbour coefficients)
-  double* G = Vn + 3 * Nst;              // kConvCH x 9 x Ng (volume) or kConvCH x 3 x Ng (faces)
+  double* acc = sm;                                          // 3 x Nst
+  float2* ViP = reinterpret_cast<float2*>(acc + 3 * Nst);    // 3 x Nst (own coefficients, pairs)
+  float2* VnP = ViP + 3 * Nst;                               // 3 x Nst (neighbour coefficients, pairs)
+  double* G = reinterpret_cast<double*>(VnP + 3 * Nst);      // kConvCH x 9 x Ng (volume) or x 3 x Ng (faces)
+  float2* GP = reinterpret_cast<float2*>(G);                 // the same, as pairs (each thread converts its own)
   const double* Ji = a.Jinv + 9 * (size_t)i;
   const double dj = a.detJ[i];
   const int u = threadIdx.x;
   for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
     acc[o] = 0.0;
     const int c = o / Nst, rem = o % Nst;
-    Vi[o] = a.vbar[((size_t)c * ne + i) * Nst + rem];
+    ViP[o] = pair_split(a.vbar[((size_t)c * ne + i) * Nst + rem]);
   }
   __syncthreads();
   // volume term: - int grad(phi~_k) . F_c(vbar)
@@ -328,16 +361,16 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
     const int cnt = min(kConvCH, a.nq - base);
     if (u < cnt) {
       const int q = base + u;
-      const double* ph = a.phi + (size_t)q * N;
+      const float2* ph = phiP + (size_t)q * N;
       double S[3][kMaxNg];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int b = 0; b < kMaxNg; ++b) {
-          double sb = 0.0;
+          float ss = 0.0f, cc = 0.0f;
           if (b < Ng)
-            for (int k = 0; k < N; ++k) sb = fma(ph[k], Vi[c * Nst + b * N + k], sb);
-          S[c][b] = sb;
+            for (int k = 0; k < N; ++k) pair_fma(ph[k], ViP[c * Nst + b * N + k], ss, cc);
+          S[c][b] = pair_value(ss, cc);
         }
       double* Gu = G + (size_t)u * 9 * Ng;
       for (int e = 0; e < 9 * Ng; ++e) Gu[e] = 0.0;
@@ -361,17 +394,21 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
             for (int ta = 0; ta < Ng; ++ta) Gu[(c * 3 + e) * Ng + ta] = fma(g[ta], h, Gu[(c * 3 + e) * Ng + ta]);
           }
       }
+      float2* GPu = GP + (size_t)u * 9 * Ng;
+      for (int e = 0; e < 9 * Ng; ++e) GPu[e] = pair_split(Gu[e]);
     }
     __syncthreads();
     for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
       const int c = o / Nst, rem = o % Nst, ta = rem / N, k = rem % N;
-      double s = 0.0;
+      float ss = 0.0f, cc = 0.0f;
       for (int v = 0; v < cnt; ++v) {
-        const double* dp = a.dphi + (size_t)(base + v) * 3 * N + k;
-        const double* Gv = G + (size_t)v * 9 * Ng + c * 3 * Ng + ta;
-        s = fma(Gv[0], dp[0], fma(Gv[Ng], dp[N], fma(Gv[2 * Ng], dp[2 * N], s)));
+        const float2* dp = dphiP + (size_t)(base + v) * 3 * N + k;
+        const float2* Gv = GP + (size_t)v * 9 * Ng + c * 3 * Ng + ta;
+        pair_fma(Gv[0], dp[0], ss, cc);
+        pair_fma(Gv[Ng], dp[N], ss, cc);
+        pair_fma(Gv[2 * Ng], dp[2 * N], ss, cc);
       }
-      acc[o] -= s;
+      acc[o] -= pair_value(ss, cc);
     }
     __syncthreads();
   }
@@ -388,7 +425,7 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
     if (nb >= 0) {
       for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
         const int c = o / Nst, rem = o % Nst;
-        Vn[o] = a.vbar[((size_t)c * ne + nb) * Nst + rem];
+        VnP[o] = pair_split(a.vbar[((size_t)c * ne + nb) * Nst + rem]);
       }
     }
     __syncthreads();
@@ -396,28 +433,28 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
       const int cnt = min(kConvCH, a.nqf - base);
       if (u < cnt) {
         const int q = base + u;
-        const double* ph = a.fphi + ((size_t)code * a.nqf + q) * N;
+        const float2* ph = fphiP + ((size_t)code * a.nqf + q) * N;
         double Sm[3][kMaxNg], Sp[3][kMaxNg];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int b = 0; b < kMaxNg; ++b) {
-            double sb = 0.0;
+            float ss = 0.0f, cc = 0.0f;
             if (b < Ng)
-              for (int k = 0; k < N; ++k) sb = fma(ph[k], Vi[c * Nst + b * N + k], sb);
-            Sm[c][b] = sb;
+              for (int k = 0; k < N; ++k) pair_fma(ph[k], ViP[c * Nst + b * N + k], ss, cc);
+            Sm[c][b] = pair_value(ss, cc);
           }
         double x[3] = {0.0, 0.0, 0.0};
         if (nb >= 0) {
-          const double* phn = a.fphi + ((size_t)codeb * a.nqf + q) * N;
+          const float2* phn = fphiP + ((size_t)codeb * a.nqf + q) * N;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int b = 0; b < kMaxNg; ++b) {
-              double sb = 0.0;
+              float ss = 0.0f, cc = 0.0f;
               if (b < Ng)
-                for (int k = 0; k < N; ++k) sb = fma(phn[k], Vn[c * Nst + b * N + k], sb);
-              Sp[c][b] = sb;
+                for (int k = 0; k < N; ++k) pair_fma(phn[k], VnP[c * Nst + b * N + k], ss, cc);
+              Sp[c][b] = pair_value(ss, cc);
             }
         } else {
           const double s = a.tri_st[2 * q], t = a.tri_st[2 * q + 1];
@@ -459,14 +496,16 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a) {
             for (int ta = 0; ta < Ng; ++ta) Gu[c * Ng + ta] = fma(g[ta], h, Gu[c * Ng + ta]);
           }
         }
+        float2* GPu = GP + (size_t)u * 3 * Ng;
+        for (int e = 0; e < 3 * Ng; ++e) GPu[e] = pair_split(Gu[e]);
       }
       __syncthreads();
       for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
         const int c = o / Nst, rem = o % Nst, ta = rem / N, k = rem % N;
-        double s = 0.0;
+        float ss = 0.0f, cc = 0.0f;
         for (int v = 0; v < cnt; ++v)
-          s = fma(a.fphi[((size_t)code * a.nqf + base + v) * N + k], G[(size_t)v * 3 * Ng + c * Ng + ta], s);
-        acc[o] += s;
+          pair_fma(fphiP[((size_t)code * a.nqf + base + v) * N + k], GP[(size_t)v * 3 * Ng + c * Ng + ta], ss, cc);
+        acc[o] += pair_value(ss, cc);
       }
       __syncthreads();
     }
@@ -643,6 +682,16 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   cudaMemsetAsync(s->P, 0, np * sizeof(double), st);
   const size_t conv_smem = ((size_t)9 * Nst + (size_t)kConvCH * 9 * Ng) * sizeof(double);
   cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+  if (!s->cphiP) {                                  // the convection tables as binary32 pairs, once
+    const size_t n1 = (size_t)s->nq_nl * N, n2 = (size_t)s->nq_nl * 3 * N, n3 = (size_t)64 * s->nqf_nl * N;
+    if ((e = dev_alloc(s, (void**)&s->cphiP, (n1 + n2 + n3) * sizeof(float2))) != STDG_OK) return e;
+    s->cdphiP = s->cphiP + n1;
+    s->cfphiP = s->cdphiP + n2;
+    s->nlaunch += 3;
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n1, s->dr.tet_nl_phi, s->cphiP);
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n2, s->dr.tet_nl_dphi, s->cdphiP);
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n3, s->dr.face_nl_phi, s->cfphiP);
+  }
   phase_mark(s, 0);
   for (int k = 0; k < n_picard; ++k) {
     // 1. averaging and previous-Picard pressure gradient
@@ -666,7 +715,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
                 s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
                 s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, to_arg(s->bc), s->t, s->dt, s->Vbar, s->Ups};
     ++s->nlaunch;
-    k_convection<<<ne, kConvCH, conv_smem, st>>>(ca);
+    k_convection<<<ne, kConvCH, conv_smem, st>>>(ca, s->cphiP, s->cdphiP, s->cfphiP);
     phase_mark(s, 2);
     // 3. viscous systems (Eq. A1_mod), one per component, initial guess vbar^{n+1,k}
     ++s->nlaunch;
