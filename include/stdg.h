@@ -149,6 +149,18 @@ stdg_status stdg_mesh_info(const stdg_mesh* mesh, int64_t* ne, int64_t* nfaces,
 stdg_status stdg_mesh_faces(const stdg_mesh* mesh, int64_t* left_host, int64_t* right_host,
                             int32_t* lface_host, int32_t* rface_host);
 
+/* Nested agglomerates of the mesh's tets: the coarse levels of STDG_SOLVER_KRON_MG.  Tet centroids
+ * are binned into cubes of edge h = cbrt(mean |det J_i|) (6 x the mean tet volume: the hexahedron
+ * edge of a Kuhn mesh) anchored at the lower corner of the vertices' bounding box, then into cubes
+ * of edge 2h, 4h, ...; a size that merges no bins is skipped; it stops at the first level with at
+ * most coarse_max cells, or after max_levels levels.  Out (caller-owned host arrays):
+ * cell_host[l * ne + i] = cell of tet i on level l + 1 (cells numbered 0, 1, ... in bin order),
+ * sizes_host[l] = cells on level l + 1, for l < *levels (arrays of max_levels * ne and max_levels
+ * entries).  STDG_EINVAL on a NULL pointer or a limit < 1; STDG_EUNSUPPORTED (outputs filled) if
+ * max_levels levels still leave more than coarse_max cells.  Host-only. */
+stdg_status stdg_mesh_agglomerate(const stdg_mesh* mesh, int coarse_max, int max_levels, int32_t* cell_host,
+                                  int64_t* sizes_host, int* levels);
+
 /* ------------------------------------------------ reference matrices (Sec. 2.3-2.4) */
 /* Quadrature rules, Dubiner / Legendre tables and the time matrices
  * K_ab = gamma_a(1) gamma_b(1) - int_0^1 gamma_a' gamma_b (from Eqs. MD_2, MD_2_2).

@@ -85,6 +85,19 @@ class Mesh:
             self._h = None
 
 
+    def agglomerate(self, coarse_max=512, max_levels=16):
+        """stdg_mesh_agglomerate: (cells [levels x ne], sizes [levels]) of the nested agglomerates."""
+        lib = _lib.load()
+        ne = self.ne
+        cell = np.empty(max_levels * ne, dtype=np.int32)
+        sizes = np.empty(max_levels, dtype=np.int64)
+        lv = C.c_int()
+        _lib.check(lib.stdg_mesh_agglomerate(self._h, int(coarse_max), int(max_levels),
+                                             cell.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             sizes.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(lv)))
+        L = lv.value
+        return cell[:L * ne].reshape(L, ne), sizes[:L]
+
 class Reference:
     """Reference quadrature / basis tables and the time matrix K (stdg_reference_matrices)."""
 

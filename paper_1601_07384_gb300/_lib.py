@@ -58,6 +58,8 @@ SIGNATURES = {
     "stdg_ref_destroy": (None, [P]),
     "stdg_ref_time_matrix": (C.c_int, [P, DP]),
     "stdg_time_blockdiag": (C.c_int, [DP, C.c_int, DP, DP, DP, C.POINTER(C.c_int)]),
+    "stdg_mesh_agglomerate": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int)]),
     "stdg_ref_eval": (C.c_int, [P, DP, C.c_int64, DP, DP]),
     "stdg_tet_rule": (C.c_int, [C.c_int, DP, DP]),
     "stdg_solver_create": (C.c_int, [P, P, C.c_double, C.POINTER(SolverOptions), P, C.POINTER(P)]),

@@ -304,6 +304,40 @@ std::vector<float> to_f32(const std::vector<double>& v) { return std::vector<flo
 
 }  // namespace
 
+// Nested agglomerates: tet centroids binned into cubes of edge h1 anchored at lo, then of edge 2 h1,
+// 4 h1, ... (a size that merges no bins is skipped), until at most coarse_max cells remain or
+// max_levels levels exist.  cell[l][i] = cell of tet i on level l + 1, numbered in bin-key order.
+// Returns false if the last level still has more than coarse_max cells.
+bool agglomerate_levels(int ne, const double* bary, const double lo[3], double h1, int coarse_max, int max_levels,
+                        std::vector<std::vector<int>>& cell, std::vector<int>& sizes) {
+  cell.clear();
+  sizes.assign(1, ne);
+  std::vector<int64_t> ic(3 * (size_t)ne);
+  for (int i = 0; i < ne; ++i)
+    for (int c = 0; c < 3; ++c)
+      ic[3 * (size_t)i + c] = std::max<int64_t>(0, (int64_t)std::floor((bary[3 * (size_t)i + c] - lo[c]) / h1));
+  for (int shift = 0; shift < 40 && (int)cell.size() < max_levels; ++shift) {
+    std::vector<std::pair<int64_t, int>> key(ne);
+    for (int i = 0; i < ne; ++i) {
+      const int64_t x = ic[3 * (size_t)i] >> shift, y = ic[3 * (size_t)i + 1] >> shift, z = ic[3 * (size_t)i + 2] >> shift;
+      key[i] = {(x << 42) | (y << 21) | z, i};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int> id(ne);
+    int n = 0;
+    for (int k = 0; k < ne; ++k) {
+      if (k > 0 && key[k].first != key[k - 1].first) ++n;
+      id[key[k].second] = n;
+    }
+    ++n;
+    if (n == sizes.back() && !cell.empty()) continue;   // no agglomeration at this size: grow the cube
+    cell.push_back(std::move(id));
+    sizes.push_back(n);
+    if (n <= coarse_max) break;
+  }
+  return !cell.empty() && sizes.back() <= coarse_max;
+}
+
 double mg_omega() {
   const char* env = std::getenv("STDG_MG_OMEGA");
   const double w = env ? std::atof(env) : 0.8;
@@ -354,33 +388,12 @@ stdg_status mg_ensure(stdg_solver* s) {
     vsum += std::fabs(detJ[i]);
   }
   const double h1 = std::cbrt(vsum / ne);       // |det J| = 6 x volume
-  std::vector<int64_t> ic(3 * (size_t)ne);
-  for (int i = 0; i < ne; ++i)
-    for (int c = 0; c < 3; ++c)
-      ic[3 * (size_t)i + c] = std::max<int64_t>(0, (int64_t)std::floor((bary[3 * (size_t)i + c] - lo[c]) / h1));
-  // cell of every tet on each level
   std::vector<std::vector<int>> cell;             // cell[l-1][tet], levels 1..L
-  std::vector<int> sizes{ne};
-  for (int shift = 0; shift < 40 && (int)cell.size() < kMgMaxLevels; ++shift) {
-    std::vector<std::pair<int64_t, int>> key(ne);
-    for (int i = 0; i < ne; ++i) {
-      const int64_t x = ic[3 * (size_t)i] >> shift, y = ic[3 * (size_t)i + 1] >> shift, z = ic[3 * (size_t)i + 2] >> shift;
-      key[i] = {(x << 42) | (y << 21) | z, i};
-    }
-    std::sort(key.begin(), key.end());
-    std::vector<int> id(ne);
-    int n = 0;
-    for (int k = 0; k < ne; ++k) {
-      if (k > 0 && key[k].first != key[k - 1].first) ++n;
-      id[key[k].second] = n;
-    }
-    ++n;
-    if (n == sizes.back() && !cell.empty()) continue;   // no agglomeration at this size: grow the cube
-    cell.push_back(std::move(id));
-    sizes.push_back(n);
-    if (n <= kCoarseMax) break;
+  std::vector<int> sizes;
+  if (!agglomerate_levels(ne, bary.data(), lo, h1, kCoarseMax, kMgMaxLevels, cell, sizes)) {
+    set_error("coarse correction: agglomeration left %d cells", sizes.back());
+    return STDG_EINVAL;
   }
-  if (sizes.back() > kCoarseMax) { set_error("coarse correction: agglomeration left %d cells", sizes.back()); return STDG_EINVAL; }
   const int L = (int)cell.size();
   MgState* mg = new MgState();
   mg->L = L;
@@ -520,3 +533,29 @@ void mg_free(stdg_solver* s) {
 }
 
 }  // namespace stdg
+
+extern "C" stdg_status stdg_mesh_agglomerate(const stdg_mesh* m, int coarse_max, int max_levels, int32_t* cell,
+                                             int64_t* sizes, int* levels) {
+  if (!m || !cell || !sizes || !levels || max_levels < 1 || coarse_max < 1) {
+    stdg::set_error("stdg_mesh_agglomerate: NULL argument or non-positive limit");
+    return STDG_EINVAL;
+  }
+  const int ne = (int)m->ne;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, vsum = 0.0;
+  for (int64_t v = 0; v < m->nv; ++v)
+    for (int c = 0; c < 3; ++c) lo[c] = std::min(lo[c], m->X[3 * v + c]);
+  for (int i = 0; i < ne; ++i) vsum += std::fabs(m->detJ[i]);
+  std::vector<std::vector<int>> cl;
+  std::vector<int> sz;
+  const bool ok = stdg::agglomerate_levels(ne, m->bary.data(), lo, std::cbrt(vsum / ne), coarse_max, max_levels, cl, sz);
+  *levels = (int)cl.size();
+  for (size_t l = 0; l < cl.size(); ++l) {
+    sizes[l] = sz[l + 1];
+    for (int i = 0; i < ne; ++i) cell[l * (size_t)ne + i] = cl[l][i];
+  }
+  if (!ok) {
+    stdg::set_error("stdg_mesh_agglomerate: %d levels leave more than %d cells", max_levels, coarse_max);
+    return STDG_EUNSUPPORTED;
+  }
+  return STDG_OK;
+}

@@ -135,3 +135,29 @@ def test_time_blockdiag_rotation_and_errors(lib):
     assert int(pair.sum()) == 1
     with pytest.raises(g.StdgError):
         g.time_blockdiag(np.eye(6))
+
+
+@pytest.mark.parametrize("n", [4, 9, 20])
+def test_agglomerates_of_a_kuhn_mesh(lib, n):
+    """stdg_mesh_agglomerate (host logic of the KRON_MG coarse correction): on the 6 n^3 jittered
+    Kuhn tets the first level is exactly each hexahedron's 6 tets, every next level the 2 x 2 x 2
+    blocks of the previous one (partly filled when n is odd), each level partitions the previous
+    one, and the last is the first with at most 512 cells."""
+    import paper_1601_07384_gb300 as g
+    from inputs import kuhn_mesh
+    v, t = kuhn_mesh(n, seed=0)
+    cells, sizes = g.Mesh(v, t).agglomerate()
+    ne = 6 * n ** 3
+    hexid = np.arange(ne) // 6                       # tet id = 6 (i + n (j + n k)) + permutation
+    hi, hj, hk = hexid % n, (hexid // n) % n, hexid // (n * n)
+    assert sizes[0] == n ** 3
+    assert len(set(zip(cells[0].tolist(), hexid.tolist()))) == n ** 3
+    for lvl in range(1, len(sizes)):
+        s = 2 ** lvl
+        m = (n + s - 1) // s
+        blk = (hi // s) + m * ((hj // s) + m * (hk // s))
+        assert len(set(blk.tolist())) == sizes[lvl]
+        assert len(set(zip(cells[lvl].tolist(), blk.tolist()))) == sizes[lvl]
+        assert len(set(zip(cells[lvl - 1].tolist(), cells[lvl].tolist()))) == sizes[lvl - 1]
+    assert sizes[-1] <= 512 and (len(sizes) == 1 or sizes[-2] > 512)
+    assert list(sizes) == {4: [64], 9: [729, 125], 20: [8000, 1000, 125]}[n]
