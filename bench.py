@@ -7,9 +7,10 @@ d = pi/2), nu = 0.01, dt = 0.005, 3 Picard iterations per step, pressure solves 
 1e-10 relative residual.  A "step" is one full time step (stdg_step: averaging, convection,
 viscous solves, pressure right-hand side, pressure solve, velocity update, 3 times).
 
-Metric: seconds per time step with the chosen solver (Kronecker-decoupled block CG), next
-to plain FP64 GMRES(50); the operator kernel's achieved throughput is reported as a
-roofline against the FP64 pipe (its bound on sm_103a) and against HBM.
+Metric: seconds per time step with the chosen solver (Kronecker-decoupled block CG with the
+agglomeration coarse correction, mixed precision by default), next to plain FP64 GMRES(50); the
+dominant operator kernel's achieved throughput is reported as a roofline (HBM for binary32
+blocks, the FP64 pipe or the derived pair-arithmetic peak for the binary64-accurate kernels).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
