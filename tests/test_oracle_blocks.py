@@ -185,3 +185,46 @@ def test_sparse_matches_matrix_free():
     assert np.allclose(A @ x.ravel(), ops.pressure_apply(d, x).ravel(), rtol=0, atol=1e-15 * np.abs(x).max())
     L = ops.viscous_sparse(d, 0.2)
     assert np.allclose(L @ x.ravel(), ops.viscous_apply(d, x, 0.2).ravel(), rtol=0, atol=1e-15 * np.abs(x).max())
+
+
+def test_viscous_kronecker_structure_and_time_decoupling():
+    """p_t = 1: the literal space-time viscous operator of Eq. A1_mod equals D (x) K + G (x) I, with
+    D = diag(|J_i|) (x) I_N the spatial mass (diagonal for the orthonormal basis) and G the spatial
+    viscous part (the p_t = 0 operator minus D; symmetric positive definite).  Consequence used by
+    the time-decoupled viscous solver: with K = W R W^-1, x = (I (x) W) y splits the system into one
+    system per eigenvalue of K, and solving those reproduces the direct solve."""
+    nu, dt = 0.2, 0.01
+    d1 = make(2, 2, 1, dt=dt)
+    d0 = make(2, 2, 0, dt=dt)
+    N, ne = d1.N, d1.mesh.ne
+    V1 = ops.viscous_sparse(d1, nu).toarray()
+    V0 = ops.viscous_sparse(d0, nu).toarray()
+    D = np.zeros_like(V0)
+    for i in range(ne):
+        Mi = d0.tet_blocks(i)["Mbar"]
+        assert np.abs(Mi - np.diag(np.diag(Mi))).max() <= 1e-14 * np.abs(Mi).max()
+        D[i * N:(i + 1) * N, i * N:(i + 1) * N] = Mi
+    G = V0 - D
+    assert np.abs(G - G.T).max() <= 1e-13 * np.abs(G).max()
+    np.linalg.cholesky(G)
+    K = K_closed(1)
+    for a in range(2):
+        for b in range(2):
+            ia = (np.arange(ne)[:, None] * 2 * N + a * N + np.arange(N)[None, :]).ravel()
+            ib = (np.arange(ne)[:, None] * 2 * N + b * N + np.arange(N)[None, :]).ravel()
+            ref = D * K[a, b] + (G if a == b else 0.0)
+            assert np.abs(V1[np.ix_(ia, ib)] - ref).max() <= 1e-13 * np.abs(V1).max()
+    # decoupling: K has the complex pair 2 +- i sqrt(2); with its eigenvectors each time mode solves
+    # (lambda D + G) y = b~ (complex symmetric), and x = W y
+    lam, Wc = np.linalg.eig(K)
+    assert np.allclose(sorted(lam, key=lambda z: z.imag), [2 - 1j * np.sqrt(2), 2 + 1j * np.sqrt(2)])
+    rhs = np.random.default_rng(7).standard_normal(ne * 2 * N)
+    x_direct = np.linalg.solve(V1, rhs)
+    B = rhs.reshape(ne, 2, N)
+    Bt = np.einsum("ab,ibk->iak", np.linalg.inv(Wc), B)
+    Y = np.zeros_like(Bt, dtype=complex)
+    for q in range(2):
+        Y[:, q, :] = np.linalg.solve(lam[q] * D + G, Bt[:, q, :].ravel()).reshape(ne, N)
+    X = np.einsum("ab,ibk->iak", Wc, Y)
+    assert np.abs(X.imag).max() <= 1e-10 * np.abs(X).max()
+    assert np.abs(X.real.ravel() - x_direct).max() <= 1e-11 * np.abs(x_direct).max()
