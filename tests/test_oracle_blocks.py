@@ -228,3 +228,27 @@ def test_viscous_kronecker_structure_and_time_decoupling():
     X = np.einsum("ab,ibk->iak", Wc, Y)
     assert np.abs(X.imag).max() <= 1e-10 * np.abs(X).max()
     assert np.abs(X.real.ravel() - x_direct).max() <= 1e-11 * np.abs(x_direct).max()
+
+
+def test_constant_mode_restriction():
+    """Premise of the KRON_MG coarse correction: Dubiner function 0 is constant on the reference tet,
+    so the piecewise-constant coarse space of a mesh is spanned by the coefficients k = 0, the
+    Galerkin restriction R (-A) R^T of the pinned pressure operator is the matrix of the (0, 0)
+    entries of its blocks, and that matrix is symmetric positive definite."""
+    from oracle.basis import dubiner
+    d = make(3, 2, 0, dt=0.01)
+    xi = tet_rule(3)[0]
+    phi, _ = dubiner(2, xi)
+    assert np.abs(phi[:, 0] - phi[0, 0]).max() <= 1e-14 and np.abs(phi[:, 1:]).max() > 0.1
+    A = -ops.pressure_dense(d, pinned=True)
+    N, ne = d.N, d.mesh.ne
+    R = np.zeros((ne, ne * N))
+    R[np.arange(ne), np.arange(ne) * N] = 1.0
+    A0 = R @ A @ R.T
+    assert np.array_equal(A0, A[::N, ::N])
+    assert np.abs(A0 - A0.T).max() <= 1e-14 * np.abs(A0).max()
+    np.linalg.cholesky(A0)
+    # a coefficient vector with only constant modes is a piecewise-constant field
+    c = np.random.default_rng(3).standard_normal(ne)
+    x = R.T @ c
+    assert np.array_equal(x.reshape(ne, N)[:, 1:], np.zeros((ne, N - 1)))
