@@ -101,9 +101,13 @@ enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_
  *                     preconditioned by a fixed number of block-Jacobi CG iterations whose
  *                     operator blocks are binary32 / bfloat16 (vectors and accumulation
  *                     binary32).  Residual recurrence, scalars and stopping test are binary64,
- *                     so the returned x meets the same FP64 residual tolerance; the viscous
- *                     solves use the STDG_PREC_DF32 operator.  stdg_solve_stats.iterations
- *                     counts the binary32 iterations and .restarts the outer ones.          */
+ *                     so the returned x meets the same FP64 residual tolerance.  With
+ *                     STDG_SOLVER_KRON_MG the inner iterations add the coarse correction.
+ *                     With STDG_PREC_MIXED_F32 the viscous solves of stdg_step are a binary64
+ *                     refinement (residual with the STDG_PREC_DF32 operator) around binary32
+ *                     inner solves; with STDG_PREC_MIXED_BF16 they use the STDG_PREC_DF32
+ *                     operator.  stdg_solve_stats.iterations counts the binary32 iterations
+ *                     and .restarts the outer ones.                                          */
 enum { STDG_PREC_FP64 = 0, STDG_PREC_DF32 = 1, STDG_PREC_MIXED_F32 = 2, STDG_PREC_MIXED_BF16 = 3 };
 
 typedef struct {
@@ -281,7 +285,12 @@ stdg_status stdg_set_initial(stdg_solver* s, const stdg_field* field);
 stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* field);
 /* One time step t -> t + dt of the Picard pressure-correction algorithm (Sec. 2.6, steps
  * 0-6), n_picard Picard iterations, viscosity nu; pressure solves with `method` to `tol`,
- * viscous solves (Eq. A1_mod) with CG (p_t = 0) or GMRES to `tol`.  stats may be NULL. */
+ * viscous solves (Eq. A1_mod) to `tol`: decoupled in time with K = W R W^-1
+ * (stdg_time_blockdiag) and solved by conjugate-orthogonal CG preconditioned by the exact
+ * inverse of every tet's diagonal block, then confirmed on the original system (GMRES iterates
+ * only if that residual is above `tol`).  STDG_VISC_SOLVER=gmres in the environment selects
+ * the previous solvers (CG for p_t = 0, right-preconditioned GMRES(20) otherwise).  stats may
+ * be NULL. */
 stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
                       stdg_step_stats* stats);
 /* Semi-implicit theta variant for p_t = 0 (Sec. 2.7, Eqs. CS_15_theta / CS_16_theta): the
