@@ -170,6 +170,19 @@ def operator_alone_ms(solver, lowprec, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def job_seconds_per_step(ms, steps, world, device="cuda"):
+    """Whole-job time of the timed region: the maximum over ranks of each rank's `ms`, and the
+    seconds per step it implies when every rank (a replica) runs `steps` steps of the same workload
+    (steps * world steps in that time).  Collective only when world > 1."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, ms_max / 1e3 / (steps * world)
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -352,12 +365,8 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = solver.profile_read()
     solver.profile(False)
-    t_dev = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-    ms = float(t_dev.item())
     # whole job: replicas each run K steps of the same workload; s/step over all steps of all ranks
-    s_per_step = ms / 1e3 / (args.steps * world)
+    ms, s_per_step = job_seconds_per_step(ms, args.steps, world)
 
     # ---- end to end through the C ABI with host buffers: every step copies its input state from
     # pinned host memory and its result back; each repeats a timed step (same input state), so the
