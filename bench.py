@@ -279,6 +279,9 @@ def main():
     ap.add_argument("--gmres-max-iters", type=int, default=5000,
                     help="iteration cap per pressure solve of the plain FP64 GMRES(50) comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--counts-out", default="",
+                    help="write this run's operator applications per step (JSON) to this path; "
+                         "profiles/bench_operator_counts.json is the copy the reference arm reads")
     ap.add_argument("--precision", default="mixed_f32", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
     ap.add_argument("--solver", default="kron_mg", choices=["kron_cg", "kron_pcg", "kron_mg", "gmres"])
     ap.add_argument("--theta", type=float, default=1.0,
@@ -499,9 +502,10 @@ def main():
                        f"family/p/p_t, scaled to {mesh_counts(w['n'])[1]:,} interior faces x {ops_per_step:.0f} "
                        f"operator applications per step; other per-step work not included")}
     if rank == 0:
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        with open(os.path.join(ROOT, "gpurun_out", f"bench_counts_{args.workload}.json"), "w") as f:
-            json.dump({"workload": workload_name(w), "operator_applications_per_step": ops_per_step}, f)
+        if args.counts_out:                      # the operator count the reference arm scales by
+            os.makedirs(os.path.dirname(os.path.abspath(args.counts_out)), exist_ok=True)
+            with open(args.counts_out, "w") as f:
+                json.dump({"workload": workload_name(w), "operator_applications_per_step": ops_per_step}, f)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -8,8 +8,8 @@ input generators in ``inputs/``).
 Everything is built literally from the paper (Tavelli & Dumbser, arXiv:1601.07384):
 space-time blocks are assembled by space-time quadrature (no Kronecker shortcut), the
 pressure operator is Sum_j D_ij M_j^-1 Q_ij (Eq. CS_19), the Picard step follows the
-paper's Sec. 2.6 steps 0-6 in order.  Readings of points the paper leaves open are
-listed in DESIGN.md ("Readings") and cited per function as R<n>.
+paper's Sec. 2.6 steps 0-6 in order.  Where the paper leaves a point open, the reading taken
+is stated in the docstring of the function that takes it and labelled R<n>.
 
 Parity pins: every function here is pinned by a ``-m "not gpu"`` test against a
 closed form, an invariant or a corollary of the paper (see tests/test_oracle_*.py).

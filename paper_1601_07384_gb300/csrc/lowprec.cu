@@ -1,4 +1,4 @@
-// Low-precision operator path (mixed-precision iterative refinement, BASELINE row a7).
+// Low-precision operator path (binary32 / bfloat16 blocks inside the mixed-precision solves).
 //
 // k_apply_lp<TB>: the five-point block operator with blocks stored in TB (binary32 or bfloat16)
 // and vectors / accumulation in binary32.  Per application it streams every block once
