@@ -377,3 +377,19 @@ def test_graph_batched_cg_matches_unbatched(batch):
     A = ops.pressure_sparse(d)
     assert np.linalg.norm(b.ravel() - A @ x.cpu().numpy()) <= 2e-11 * np.linalg.norm(b)
     assert st["iterations"] % batch == 0
+
+
+def test_step_with_previous_viscous_solvers():
+    """STDG_VISC_SOLVER=gmres selects the previous viscous solvers (CG for p_t = 0, GMRES(20)
+    right-preconditioned by the exact tet-diagonal blocks otherwise); the variable is read once per
+    process, so the FP64 step-parity tests run again in a subprocess with it set."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, STDG_VISC_SOLVER="gmres")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(root, "tests", "test_gpu_parity.py"), "-q",
+                        "-m", "gpu", "-k", "test_step_matches_oracle and fp64"],
+                       capture_output=True, text=True, timeout=900, cwd=root, env=env)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    assert "2 passed" in r.stdout
