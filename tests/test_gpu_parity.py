@@ -275,7 +275,7 @@ def test_largest_mesh_sampled_rows():
 @pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2)])
 @pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("mixed_bf16", 5e-2)])
 def test_lowprec_operator_matches_oracle(n, p, pt, prec, tol):
-    """Binary32 / bfloat16 blocks with binary32 accumulation (TMA-staged kernel): error bounded
+    """Binary32 / bfloat16 blocks with binary32 accumulation (warp-per-tet kernel): error bounded
     by the storage precision of the blocks (2^-24 / 2^-9 relative per entry)."""
     gs, d = setup(n, p, pt, precision=prec)
     x = np.random.default_rng(5).standard_normal(d.mesh.ne * d.Nst)
@@ -358,7 +358,7 @@ def test_bf16_inner_solve_still_reaches_fp64_tolerance():
 @pytest.mark.parametrize("n,p,pt", CASES)
 @pytest.mark.parametrize("pinned", [True, False])
 def test_df32_operator_matches_oracle(n, p, pt, pinned):
-    """FP64-accurate operator from binary32 pairs (TMA-staged kernel): 1e-12 like FP64."""
+    """FP64-accurate operator from binary32 pairs (warp-per-tet kernel): 1e-12 like FP64."""
     gs, d = setup(n, p, pt, precision="df32")
     x = np.random.default_rng(n + 10 * p + pt).standard_normal(d.mesh.ne * d.Nst)
     y = gs.pressure_apply(torch.from_numpy(x).cuda(), pinned=pinned).cpu().numpy()
@@ -393,3 +393,20 @@ def test_step_with_previous_viscous_solvers():
                        capture_output=True, text=True, timeout=900, cwd=root, env=env)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     assert "2 passed" in r.stdout
+
+
+@pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("df32", 1e-12)])
+def test_tma_operator_kernels_match_oracle(prec, tol, monkeypatch):
+    """STDG_OP_KERNEL=tma selects the block-staged TMA kernels, kept for comparison with the warp
+    kernels: the same operator to the same tolerances (standalone applications; the mixed solvers
+    need the warp kernels' fused p.q partials)."""
+    monkeypatch.setenv("STDG_OP_KERNEL", "tma")
+    gs, d = setup(2, 3, 1, precision=prec)
+    x = np.random.default_rng(6).standard_normal(d.mesh.ne * d.Nst)
+    if prec == "mixed_f32":
+        y = gs.pressure_apply_f32(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+        yo = ops.pressure_apply(d, x.astype(np.float32).astype(np.float64)).ravel()
+    else:
+        y = gs.pressure_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        yo = ops.pressure_apply(d, x).ravel()
+    assert rel(y, yo) <= tol
