@@ -5,6 +5,8 @@
   residual with the pressure below) is checked symbolically by the test-suite.
 * A seeded solenoidal field v0 = curl(b Psi) with a wall bump b that vanishes with its
   gradient on the unit-cube boundary (no-slip compatible), Psi a sum of 64 Fourier modes.
+* The Arnold-Beltrami-Childress flow of the paper's convergence test (Sec. 3.2, Eq. CT_1),
+  2 pi-periodic in every direction; its exactness is checked symbolically by the test-suite.
 """
 from dataclasses import dataclass
 
@@ -41,6 +43,22 @@ def beltrami_pressure(x, t, prm: BeltramiParams):
          + 2 * np.sin(a * Y + d * Z) * np.cos(a * X + d * Y) * np.exp(a * (Z + X))
          + 2 * np.sin(a * Z + d * X) * np.cos(a * Y + d * Z) * np.exp(a * (X + Y)))
     return -0.5 * a * a * s * f2
+
+
+def abc_velocity(x, t, nu):
+    """ABC flow (Eq. CT_1): u = sin z + cos y, v = sin x + cos z, w = sin y + cos x, times
+    exp(-nu t).  Velocity (..., 3) at points x (..., 3)."""
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    f = np.exp(-nu * np.asarray(t, dtype=np.float64))
+    return np.stack([(np.sin(Z) + np.cos(Y)) * f, (np.sin(X) + np.cos(Z)) * f, (np.sin(Y) + np.cos(X)) * f], axis=-1)
+
+
+def abc_pressure(x, t, nu):
+    """Kinematic pressure of the ABC flow (Eq. CT_1), up to a constant:
+    -(cos x sin y + sin x cos z + sin z cos y) exp(-2 nu t)."""
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    f = np.exp(-2.0 * nu * np.asarray(t, dtype=np.float64))
+    return -(np.cos(X) * np.sin(Y) + np.sin(X) * np.cos(Z) + np.sin(Z) * np.cos(Y)) * f
 
 
 class SolenoidalModes:

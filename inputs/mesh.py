@@ -68,3 +68,37 @@ def kuhn_mesh(n: int, seed: int = 0, jitter: float = 0.1):
         for v, o in enumerate(offs):
             tets[:, s, v] = (hi + o[0]) + m * ((hj + o[1]) + m * (hk + o[2]))
     return verts, tets.reshape(-1, 4)
+
+
+def kuhn_periodic_mesh(n: int, lo: float = -np.pi, length: float = 2.0 * np.pi):
+    """Regular Kuhn mesh of the periodic box [lo, lo + length)^3 (the domain of the paper's
+    convergence test, Sec. 3.2): n^3 hexahedra x 6 tetrahedra with the split and tet ids of
+    kuhn_mesh, on the n^3 lattice points of the box, vertex id i + n (j + n k), lattice
+    indices taken modulo n (the vertices on the far faces are the periodic images of those on
+    the near faces).  Returns (verts[n^3, 3], tets[6 n^3, 4], period[3]); the geometry of a
+    tetrahedron is its vertices' nearest periodic images to its first vertex.  n >= 3."""
+    if n < 3:
+        raise ValueError("a periodic Kuhn mesh needs n >= 3")
+    h = length / n
+    kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    verts = lo + h * np.stack([ii, jj, kk], axis=1).astype(np.float64)
+    perms = list(permutations(range(3)))
+    local = []
+    for pi in perms:
+        o0 = np.zeros(3, dtype=np.int64)
+        o1 = o0.copy(); o1[pi[0]] += 1
+        o2 = o1.copy(); o2[pi[1]] += 1
+        o3 = np.ones(3, dtype=np.int64)
+        det = np.linalg.det(np.stack([o1 - o0, o2 - o0, o3 - o0]).astype(np.float64))
+        if det < 0:
+            o2, o3 = o3, o2
+        local.append((o0, o1, o2, o3))
+    hk, hj, hi = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()
+    tets = np.empty((n ** 3, 6, 4), dtype=np.int64)
+    for s, offs in enumerate(local):
+        for v, o in enumerate(offs):
+            tets[:, s, v] = (hi + o[0]) % n + n * (((hj + o[1]) % n) + n * ((hk + o[2]) % n))
+    return verts, tets.reshape(-1, 4), np.full(3, length)
+

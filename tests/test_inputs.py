@@ -43,3 +43,42 @@ def test_solenoidal_modes_divergence_free_and_no_slip():
     g = np.linspace(0, 1, 33)
     P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
     assert abs(np.linalg.norm(f(P), axis=1).max() - 0.1) < 1e-12
+
+
+def test_abc_is_exact_navier_stokes():
+    """Eq. CT_1 (the paper's convergence test): divergence-free, and with the stated pressure the
+    momentum residual of the incompressible Navier-Stokes equations vanishes for any nu."""
+    sp = pytest.importorskip("sympy")
+    from inputs import abc_pressure, abc_velocity
+    x, y, z, t, nu = sp.symbols("x y z t nu")
+    f = sp.exp(-nu * t)
+    V = [(sp.sin(z) + sp.cos(y)) * f, (sp.sin(x) + sp.cos(z)) * f, (sp.sin(y) + sp.cos(x)) * f]
+    p = -(sp.cos(x) * sp.sin(y) + sp.sin(x) * sp.cos(z) + sp.sin(z) * sp.cos(y)) * sp.exp(-2 * nu * t)
+    X = [x, y, z]
+    assert sp.simplify(sum(sp.diff(V[i], X[i]) for i in range(3))) == 0
+    for i in range(3):
+        r = (sp.diff(V[i], t) + sum(V[j] * sp.diff(V[i], X[j]) for j in range(3)) + sp.diff(p, X[i])
+             - nu * sum(sp.diff(V[i], X[j], 2) for j in range(3)))
+        assert sp.simplify(sp.expand_trig(r)) == 0
+    pt = np.array([0.3, -1.1, 2.0]); tt, nuv = 0.7, 0.4
+    sub = {x: pt[0], y: pt[1], z: pt[2], t: tt, nu: nuv}
+    assert np.allclose(abc_velocity(pt[None], tt, nuv)[0], [float(c.subs(sub)) for c in V], atol=1e-14)
+    assert abs(abc_pressure(pt[None], tt, nuv)[0] - float(p.subs(sub))) < 1e-14
+
+
+def test_periodic_kuhn_mesh():
+    """Lattice vertices of the periodic box, positively oriented tetrahedra of volume h^3 / 6 once
+    unwrapped, and every face shared by exactly two tetrahedra."""
+    from inputs import kuhn_periodic_mesh
+    n = 3
+    v, t, per = kuhn_periodic_mesh(n)
+    assert v.shape == (n ** 3, 3) and t.shape == (6 * n ** 3, 4) and np.allclose(per, 2 * np.pi)
+    P = v[t]
+    P = P[:, :1] + (P - P[:, :1]) - per * np.round((P - P[:, :1]) / per)
+    vol = np.linalg.det(np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], -1)) / 6
+    assert np.allclose(vol, (2 * np.pi / n) ** 3 / 6)
+    faces = {}
+    for i, tt in enumerate(t):
+        for f in range(4):
+            faces.setdefault(tuple(sorted(np.delete(tt, f))), []).append(i)
+    assert all(len(l) == 2 for l in faces.values()) and len(faces) == 2 * len(t)
