@@ -98,7 +98,7 @@ class SpaceTimeDG:
         tau, wt = self.time_lin
         gv, gd = self.gamma(tau)
         n_j = m.normal[j]
-        fx, fw = map_tri(m.X[m.fverts[j]], *self.tri_lin)
+        fx, fw = map_tri(m.face_coords(j), *self.tri_lin)
         out = {"sides": [], "Q": [], "D": [], "Mij": [], "Qvol": []}
         Mp = np.zeros((Nst, Nst)); Mo = np.zeros((Nst, Nst)); Mbar = np.zeros((Nst, Nst))
         for i, V in m.dual_subtets(j):
@@ -150,7 +150,7 @@ class SpaceTimeDG:
         m, dt = self.mesh, self.dt
         tau, wt = self.time_lin
         gv, gd = self.gamma(tau)
-        x, w = map_tet(m.X[m.T[i]], *self.tet_lin)
+        x, w = map_tet(m.tet_coords(i), *self.tet_lin)
         ph, _ = self.phi(i, x)
         W = np.kron(w, wt) * dt
         Fst = st_table(ph, gv)

@@ -7,16 +7,26 @@
 * Dual cell of interior face j: H_j = T_{l,j} U T_{r,j}, T_{i,j} = tetrahedron spanned by
   face j and the barycentre of T_i.  A boundary face's dual cell is T_{i,j} (reading R2).
 * The canonical vertex order (A, B, C) of face j is l(j)'s local order.
+* Periodic meshes (period given): vertex ids are the lattice points of the periodic box, a
+  tetrahedron's geometry is its vertices' periodic images nearest to its first vertex, faces
+  are matched by vertex ids (so every face is interior), and face geometry is taken in l(j)'s
+  frame.  Points are mapped into a tetrahedron's reference coordinates through the periodic
+  image nearest to it, so basis functions of r(j) can be evaluated at points given in l(j)'s
+  frame.
 """
 import numpy as np
 
 
 class Mesh:
-    def __init__(self, verts, tets):
+    def __init__(self, verts, tets, period=None):
         self.X = np.asarray(verts, dtype=np.float64)
         self.T = np.asarray(tets, dtype=np.int64)
+        self.period = None if period is None else np.asarray(period, dtype=np.float64)
         ne = self.T.shape[0]
         P = self.X[self.T]                                   # (ne, 4, 3)
+        if self.period is not None:                          # nearest images to the first vertex
+            P = P[:, :1] + self.min_image(P - P[:, :1])
+        self.P = P
         self.J = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=-1)
         self.detJ = np.linalg.det(self.J)
         if np.any(self.detJ <= 0):
@@ -53,22 +63,40 @@ class Mesh:
             if r >= 0:
                 self.t2f[r, fr] = j
                 self.t2n[r, fr] = l
-        # canonical face vertices: l's local order, skipping local vertex fl
+        # canonical face vertices: l's local order, skipping local vertex fl (coordinates in l's frame)
         self.fverts = np.array([[self.T[l, k] for k in range(4) if k != fl]
                                 for (l, fl, _, _) in recs])
-        A, B, C = (self.X[self.fverts[:, k]] for k in range(3))
+        self.fcoords = np.array([[P[l, k] for k in range(4) if k != fl] for (l, fl, _, _) in recs])
+        A, B, C = (self.fcoords[:, k] for k in range(3))
         cr = np.cross(B - A, C - A)
         self.area = 0.5 * np.linalg.norm(cr, axis=1)
         n = cr / (2.0 * self.area[:, None])
-        opp = self.X[self.T[self.left, self.fl]]
+        opp = P[self.left, self.fl]
         flip = np.einsum("jd,jd->j", n, opp - A) > 0      # must point away from l's opposite vertex
         n[flip] *= -1.0
         self.normal = n
 
+    def min_image(self, d):
+        """Displacements d (..., 3) replaced by their periodic images nearest to 0 (identity for a
+        non-periodic mesh)."""
+        d = np.asarray(d, dtype=np.float64)
+        return d if self.period is None else d - self.period * np.round(d / self.period)
+
+    def tet_coords(self, i):
+        """Vertex coordinates (4,3) of tet i (its own frame)."""
+        return self.P[i]
+
+    def face_coords(self, j):
+        """Canonical vertex coordinates (3,3) of face j, in l(j)'s frame."""
+        return self.fcoords[j]
+
     # ---- dual grid -------------------------------------------------------------------
     def subtet(self, i, j):
-        """Vertices (4,3) of T_{i,j}: canonical face vertices of j, then barycentre of i."""
-        return np.vstack([self.X[self.fverts[j]], self.bary[i][None, :]])
+        """Vertices (4,3) of T_{i,j}: canonical face vertices of j, then barycentre of i (for a
+        periodic face, r(j)'s barycentre is taken at its image next to the face)."""
+        F = self.fcoords[j]
+        b = F[0] + self.min_image(self.bary[i] - F[0])
+        return np.vstack([F, b[None, :]])
 
     def dual_subtets(self, j):
         """[(side tet id, vertices)] making up the dual cell of face j."""
@@ -95,5 +123,6 @@ class Mesh:
         return 1.0 if i == self.left[j] else -1.0
 
     def to_ref(self, i, x):
-        """Reference coordinates of physical points x (m,3) in tet i."""
-        return (np.asarray(x) - self.X[self.T[i, 0]]) @ self.Jinv[i].T
+        """Reference coordinates of physical points x (m,3) in tet i (through their periodic
+        images nearest to tet i on a periodic mesh)."""
+        return self.min_image(np.asarray(x) - self.P[i, 0]) @ self.Jinv[i].T

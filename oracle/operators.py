@@ -194,7 +194,7 @@ def convection(disc: SpaceTimeDG, vbar, t0, vbc):
     out = np.zeros((m.ne, 3, disc.Nst))
     fref = disc.tri_nl
     for i in range(m.ne):
-        x, w = map_tet(m.X[m.T[i]], *disc.tet_nl)
+        x, w = map_tet(m.tet_coords(i), *disc.tet_nl)
         ph, dph = disc.phi(i, x)
         Fst = st_table(ph, gv)
         W = np.kron(w, wt) * dt
@@ -204,7 +204,7 @@ def convection(disc: SpaceTimeDG, vbar, t0, vbc):
                 out[i, c] -= st_table(dph[:, :, d], gv).T @ (W * v[:, c] * v[:, d])
         for f in range(4):
             j = m.t2f[i, f]
-            fx, fw = map_tri(m.X[m.fverts[j]], *fref)
+            fx, fw = map_tri(m.face_coords(j), *fref)
             n_out = m.normal[j] * m.sigma(i, j)
             phf, _ = disc.phi(i, fx)
             Ff = st_table(phf, gv)
@@ -263,7 +263,7 @@ def boundary_data(disc: SpaceTimeDG, t0, vbc):
         W = np.kron(w, wt) * dt
         vq = vbc(np.repeat(x, len(tau), axis=0), np.tile(t0 + tau * dt, len(x)))
         Vbc[j] = np.linalg.solve(fb["Mbar"], (Pst * W[:, None]).T @ vq).T
-        fx, fw = map_tri(m.X[m.fverts[j]], *disc.tri_nl)
+        fx, fw = map_tri(m.face_coords(j), *disc.tri_nl)
         Pf = st_table(disc.psi(j, fx), gv)
         Wf = np.kron(fw, wt) * dt
         vf = vbc(np.repeat(fx, len(tau), axis=0), np.tile(t0 + tau * dt, len(fx)))

@@ -1,0 +1,90 @@
+"""Pins for the oracle on periodic meshes: the ABC-flow convergence test of the paper (Sec. 3.2,
+Eq. CT_1, Table 1) on [-pi, pi)^3 with periodic boundaries everywhere."""
+import numpy as np
+import pytest
+
+from inputs import abc_pressure, abc_velocity, kuhn_periodic_mesh
+from oracle import operators as ops
+from oracle.blocks import SpaceTimeDG, map_tet
+from oracle.mesh import Mesh
+from oracle.step import initial_state, time_step
+
+
+def make(n, p, pt, dt):
+    v, t, per = kuhn_periodic_mesh(n)
+    return SpaceTimeDG(Mesh(v, t, period=per), p, pt, dt)
+
+
+def test_periodic_faces_and_dual_cells():
+    """Every face is interior (2 N_e faces), its normal points from l(j) towards r(j)'s image
+    next to it, and the dual cells tile the periodic box."""
+    d = make(3, 1, 0, 0.05)
+    m = d.mesh
+    assert m.interior.all() and m.nf == 2 * m.ne
+    vol = 0.0
+    for j in range(m.nf):
+        (_, Vl), (_, Vr) = m.dual_subtets(j)
+        assert np.dot(m.normal[j], Vr[3] - Vl[3]) > 0
+        vol += sum(abs(np.linalg.det((V[1:] - V[0]).T)) / 6 for V in (Vl, Vr))
+    assert abs(vol - (2 * np.pi) ** 3) < 1e-10
+
+
+def test_periodic_constant_null_space():
+    """Without the pin, constants are the null space of the periodic pressure operator."""
+    d = make(3, 2, 1, 0.05)
+    ne, N, Ng = d.mesh.ne, d.N, d.Ng
+    P = np.zeros((ne, d.Nst))
+    for i in range(ne):                            # constant 1 in every time function
+        x, w = map_tet(d.mesh.tet_coords(i), *d.tet_nl)
+        ph, _ = d.phi(i, x)
+        c = np.linalg.solve(ph.T @ (w[:, None] * ph), ph.T @ w)
+        for a in range(Ng):
+            P[i, a * N:(a + 1) * N] = c
+    y = ops.pressure_apply(d, P, pinned=False)
+    A = ops.pressure_sparse(d, pinned=False)
+    assert np.abs(y).max() <= 1e-12 * abs(A).max() * np.abs(P).max()
+
+
+def test_periodic_free_stream_and_divergence():
+    """A uniform velocity stays uniform with zero pressure; with ABC data a step leaves the
+    discrete divergence at rounding level."""
+    d = make(3, 1, 1, 0.05)
+    u = np.array([0.7, -0.4, 0.2])
+    const = lambda x, t=0.0: np.tile(u, (len(x), 1))
+    st = initial_state(d, const)
+    V0 = st.V.copy()
+    st = time_step(d, st, 0.0, 2, const, method="direct")
+    assert np.abs(st.V - V0).max() < 1e-12 and np.abs(st.P).max() < 1e-10
+    st = initial_state(d, lambda x: abc_velocity(x, 0.0, 1.0))
+    st = time_step(d, st, 1.0, 2, lambda x, t: abc_velocity(x, t, 1.0), method="direct")
+    assert np.abs(ops.divergence(d, st.V)).max() < 1e-12
+
+
+def _pressure_error(d, st):
+    """L2 error of the pressure at t, the constant removed from both by their means (Sec. 3.2:
+    the exact pressure is defined up to a constant, chosen from the numerical mean)."""
+    ws, ph_all, pe_all = [], [], []
+    for i in range(d.mesh.ne):
+        x, w = map_tet(d.mesh.tet_coords(i), *d.tet_nl)
+        ph, _ = d.phi(i, x)
+        ph_all.append(ph @ (d.g1 @ st.P[i].reshape(d.Ng, d.N)))
+        pe_all.append(abc_pressure(x, st.t, 0.0))
+        ws.append(w)
+    w, a, b = np.concatenate(ws), np.concatenate(ph_all), np.concatenate(pe_all)
+    a = a - (w * a).sum() / w.sum()
+    b = b - (w * b).sum() / w.sum()
+    return np.sqrt((w * (a - b) ** 2).sum())
+
+
+def test_steady_abc_pressure_order_p1():
+    """Steady ABC flow (nu = 0, p = 1, p_t = 0): the pressure error decays at order >= 1.7 on
+    n = 3, 4, 6 (Table 1 reports 2.0 for p = 1)."""
+    errs = []
+    for n in (3, 4, 6):
+        d = make(n, 1, 0, 0.05)
+        st = initial_state(d, lambda x: abc_velocity(x, 0.0, 0.0))
+        for _ in range(2):
+            st = time_step(d, st, 0.0, 2, lambda x, t: abc_velocity(x, t, 0.0), method="direct")
+        errs.append(_pressure_error(d, st))
+    orders = [np.log(errs[0] / errs[1]) / np.log(4 / 3), np.log(errs[1] / errs[2]) / np.log(6 / 4)]
+    assert min(orders) >= 1.7, (errs, orders)
