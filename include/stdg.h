@@ -145,6 +145,14 @@ typedef struct { int kind; double c[3]; double a, d, nu; } stdg_field;
  * as are zero volumes and faces shared by more than two tets).  Host-only; no GPU needed. */
 stdg_status stdg_mesh_create(const double* verts_host, int64_t nv, const int64_t* tets_host,
                              int64_t ne, stdg_mesh** out);
+/* The same for a periodic box (the convergence test of Sec. 3.2): verts_host are the nv lattice
+ * points of the box, tets_host index them (a vertex on a far face is the periodic image of one
+ * on the near face), period_host[3] > 0 the box lengths.  A tet's geometry is its vertices'
+ * periodic images nearest to its first vertex; faces are matched by vertex ids, so every face is
+ * interior; face geometry is taken in l(j)'s frame.  Host-only.  A periodic mesh is not yet
+ * accepted by stdg_solver_create (STDG_EUNSUPPORTED). */
+stdg_status stdg_mesh_create_periodic(const double* verts_host, int64_t nv, const int64_t* tets_host,
+                                      int64_t ne, const double* period_host, stdg_mesh** out);
 void stdg_mesh_destroy(stdg_mesh* mesh);
 stdg_status stdg_mesh_info(const stdg_mesh* mesh, int64_t* ne, int64_t* nfaces,
                            int64_t* ninterior, int64_t* nboundary);

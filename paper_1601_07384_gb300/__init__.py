@@ -59,13 +59,19 @@ def time_blockdiag(K):
 class Mesh:
     """Primary tetrahedral mesh and its face-based dual grid (stdg_mesh_create)."""
 
-    def __init__(self, verts, tets):
+    def __init__(self, verts, tets, period=None):
         lib = _lib.load()
         v = np.ascontiguousarray(verts, dtype=np.float64)
         t = np.ascontiguousarray(tets, dtype=np.int64)
         h = C.c_void_p()
-        _lib.check(lib.stdg_mesh_create(v.ctypes.data_as(_lib.DP), v.shape[0], t.ctypes.data_as(_lib.I64P),
-                                        t.shape[0], C.byref(h)))
+        if period is None:
+            _lib.check(lib.stdg_mesh_create(v.ctypes.data_as(_lib.DP), v.shape[0], t.ctypes.data_as(_lib.I64P),
+                                            t.shape[0], C.byref(h)))
+        else:
+            per = np.ascontiguousarray(period, dtype=np.float64)
+            _lib.check(lib.stdg_mesh_create_periodic(v.ctypes.data_as(_lib.DP), v.shape[0],
+                                                     t.ctypes.data_as(_lib.I64P), t.shape[0],
+                                                     per.ctypes.data_as(_lib.DP), C.byref(h)))
         self._h = h
         ne, nf, ni, nb = (C.c_int64() for _ in range(4))
         _lib.check(lib.stdg_mesh_info(h, C.byref(ne), C.byref(nf), C.byref(ni), C.byref(nb)))

@@ -51,6 +51,7 @@ DP = C.POINTER(C.c_double)
 # name -> (restype, argtypes)
 SIGNATURES = {
     "stdg_mesh_create": (C.c_int, [DP, C.c_int64, I64P, C.c_int64, C.POINTER(P)]),
+    "stdg_mesh_create_periodic": (C.c_int, [DP, C.c_int64, I64P, C.c_int64, DP, C.POINTER(P)]),
     "stdg_mesh_destroy": (None, [P]),
     "stdg_mesh_info": (C.c_int, [P, I64P, I64P, I64P, I64P]),
     "stdg_mesh_faces": (C.c_int, [P, I64P, I64P, I32P, I32P]),

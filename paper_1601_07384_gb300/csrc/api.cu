@@ -54,6 +54,10 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
                                           const stdg_solver_options* opts, void* stream, stdg_solver** out) {
   if (!m || !r || !out || !(dt > 0.0)) { set_error("stdg_solver_create: invalid argument"); return STDG_EINVAL; }
   *out = nullptr;
+  if (m->periodic) {                      // the device kernels map points without periodic images
+    set_error("stdg_solver_create: periodic meshes are supported by the host mesh only (not yet by the solver)");
+    return STDG_EUNSUPPORTED;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     set_error("stdg_solver_create: no CUDA device available (this library has no CPU path)");
@@ -120,7 +124,7 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
     for (int c = 0; c < 3; ++c) X0[3 * i + c] = m->X[3 * m->T[4 * i] + c];
   for (int64_t j = 0; j < m->nf; ++j)
     for (int k = 0; k < 3; ++k)
-      for (int c = 0; c < 3; ++c) fvx[9 * j + 3 * k + c] = m->X[3 * m->fverts[3 * j + k] + c];
+      for (int c = 0; c < 3; ++c) fvx[9 * j + 3 * k + c] = m->fcoords[9 * j + 3 * k + c];
   TRY(upload(s, &d.X0, X0.data(), X0.size()));
   TRY(upload(s, &d.J, m->J.data(), m->J.size()));
   TRY(upload(s, &d.Jinv, m->Jinv.data(), m->Jinv.size()));

@@ -49,6 +49,9 @@ struct stdg_mesh {
   std::vector<double> normal, area;      // nf*3, nf
   std::vector<int64_t> t2f, t2n;         // ne*4
   std::vector<int32_t> t2code;           // ne*4: code of face t2f[i][f]'s canonical vertices in tet i
+  bool periodic = false;                 // periodic box: vertex ids are lattice points of the box
+  double period[3] = {0, 0, 0};
+  std::vector<double> fcoords;           // nf*9: canonical face vertex coordinates in l(j)'s frame
 };
 
 struct stdg_ref {

@@ -4,7 +4,10 @@
 //  * faces ordered by (l(j), local face of l(j)); local face f = face opposite local vertex f;
 //  * n_j: unit normal pointing from l(j) to r(j) (outward on the boundary);
 //  * canonical vertex order of face j = l(j)'s local order; code_l / code_r record where
-//    those three vertices sit among the local vertices of l and r (ordered-triple code).
+//    those three vertices sit among the local vertices of l and r (ordered-triple code);
+//  * periodic meshes: a tet's geometry is its vertices' periodic images nearest to its first
+//    vertex, faces are matched by vertex ids (every face interior), face geometry is in l(j)'s
+//    frame.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -31,8 +34,8 @@ struct KeyHash {
 struct Rec { int64_t l; int fl; int64_t r; int fr; };
 }  // namespace
 
-extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const int64_t* tets,
-                                        int64_t ne, stdg_mesh** out) {
+static stdg_status mesh_build(const double* verts, int64_t nv, const int64_t* tets, int64_t ne,
+                              const double* period, stdg_mesh** out) {
   if (!out || !verts || !tets || nv <= 0 || ne <= 0) {
     set_error("stdg_mesh_create: invalid argument");
     return STDG_EINVAL;
@@ -43,6 +46,17 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
   M->nv = nv; M->ne = ne;
   M->X.assign(verts, verts + 3 * nv);
   M->T.assign(tets, tets + 4 * ne);
+  if (period) {
+    M->periodic = true;
+    for (int d = 0; d < 3; ++d) M->period[d] = period[d];
+  }
+  // coordinate d of local vertex k of tet i (periodic: the image nearest to the tet's vertex 0)
+  auto vc = [M](int64_t i, int k, int d) {
+    const double v = M->X[3 * M->T[4 * i + k] + d];
+    if (!M->periodic || k == 0) return v;
+    const double v0 = M->X[3 * M->T[4 * i] + d], L = M->period[d];
+    return v0 + (v - v0) - L * std::nearbyint((v - v0) / L);
+  };
   M->J.resize(9 * ne); M->Jinv.resize(9 * ne); M->detJ.resize(ne); M->bary.resize(3 * ne);
   for (int64_t i = 0; i < ne; ++i) {
     const int64_t* t = &M->T[4 * i];
@@ -51,10 +65,9 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
         delete M; set_error("stdg_mesh_create: tet %lld has vertex id out of range", (long long)i);
         return STDG_EMESH;
       }
-    const double* P0 = &M->X[3 * t[0]];
     double* J = &M->J[9 * i];
     for (int c = 0; c < 3; ++c)
-      for (int d = 0; d < 3; ++d) J[d * 3 + c] = M->X[3 * t[c + 1] + d] - P0[d];  // column c = edge c
+      for (int d = 0; d < 3; ++d) J[d * 3 + c] = vc(i, c + 1, d) - vc(i, 0, d);  // column c = edge c
     double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
                  J[2] * (J[3] * J[7] - J[4] * J[6]);
     if (!(det > 0.0)) {
@@ -68,8 +81,7 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
     Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
     Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
     Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
-    for (int d = 0; d < 3; ++d)
-      M->bary[3 * i + d] = 0.25 * (M->X[3 * t[0] + d] + M->X[3 * t[1] + d] + M->X[3 * t[2] + d] + M->X[3 * t[3] + d]);
+    for (int d = 0; d < 3; ++d) M->bary[3 * i + d] = 0.25 * (vc(i, 0, d) + vc(i, 1, d) + vc(i, 2, d) + vc(i, 3, d));
   }
   std::unordered_map<Key, int64_t, KeyHash> idx;
   idx.reserve((size_t)(2.2 * ne) + 16);
@@ -102,7 +114,7 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
   M->nf = nf;
   M->left.resize(nf); M->right.resize(nf); M->fl.resize(nf); M->fr.resize(nf);
   M->fverts.resize(3 * nf); M->code_l.resize(nf); M->code_r.resize(nf);
-  M->normal.resize(3 * nf); M->area.resize(nf);
+  M->normal.resize(3 * nf); M->area.resize(nf); M->fcoords.resize(9 * nf);
   M->t2f.assign(4 * ne, -1); M->t2n.assign(4 * ne, -1); M->t2code.assign(4 * ne, -1);
   for (int64_t j = 0; j < nf; ++j) {
     const Rec& r = recs[j];
@@ -129,16 +141,18 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
       M->code_r[j] = -1;
       M->nbd++;
     }
-    const double* A = &M->X[3 * M->fverts[3 * j]];
-    const double* B = &M->X[3 * M->fverts[3 * j + 1]];
-    const double* C = &M->X[3 * M->fverts[3 * j + 2]];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) M->fcoords[9 * j + 3 * k + d] = vc(r.l, lv[k], d);
+    const double* A = &M->fcoords[9 * j];
+    const double* B = &M->fcoords[9 * j + 3];
+    const double* C = &M->fcoords[9 * j + 6];
     double e1[3], e2[3], n[3];
     for (int d = 0; d < 3; ++d) { e1[d] = B[d] - A[d]; e2[d] = C[d] - A[d]; }
     n[0] = e1[1] * e2[2] - e1[2] * e2[1];
     n[1] = e1[2] * e2[0] - e1[0] * e2[2];
     n[2] = e1[0] * e2[1] - e1[1] * e2[0];
     double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    const double* O = &M->X[3 * M->T[4 * r.l + r.fl]];  // l's vertex opposite the face
+    const double O[3] = {vc(r.l, r.fl, 0), vc(r.l, r.fl, 1), vc(r.l, r.fl, 2)};  // l's vertex opposite the face
     double s = (O[0] - A[0]) * n[0] + (O[1] - A[1]) * n[1] + (O[2] - A[2]) * n[2];
     double sg = s > 0 ? -1.0 : 1.0;
     for (int d = 0; d < 3; ++d) M->normal[3 * j + d] = sg * n[d] / len;
@@ -146,6 +160,20 @@ extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const i
   }
   *out = M;
   return STDG_OK;
+}
+
+extern "C" stdg_status stdg_mesh_create(const double* verts, int64_t nv, const int64_t* tets,
+                                        int64_t ne, stdg_mesh** out) {
+  return mesh_build(verts, nv, tets, ne, nullptr, out);
+}
+
+extern "C" stdg_status stdg_mesh_create_periodic(const double* verts, int64_t nv, const int64_t* tets,
+                                                 int64_t ne, const double* period, stdg_mesh** out) {
+  if (!period || !(period[0] > 0.0) || !(period[1] > 0.0) || !(period[2] > 0.0)) {
+    set_error("stdg_mesh_create_periodic: the period must be positive in every direction");
+    return STDG_EINVAL;
+  }
+  return mesh_build(verts, nv, tets, ne, period, out);
 }
 
 extern "C" void stdg_mesh_destroy(stdg_mesh* m) { delete m; }

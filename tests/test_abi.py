@@ -161,3 +161,25 @@ def test_agglomerates_of_a_kuhn_mesh(lib, n):
         assert len(set(zip(cells[lvl - 1].tolist(), cells[lvl].tolist()))) == sizes[lvl - 1]
     assert sizes[-1] <= 512 and (len(sizes) == 1 or sizes[-2] > 512)
     assert list(sizes) == {4: [64], 9: [729, 125], 20: [8000, 1000, 125]}[n]
+
+
+def test_periodic_mesh_matches_oracle(lib):
+    """stdg_mesh_create_periodic: the same face table as the oracle's periodic mesh (every face
+    interior), and a solver refuses it with STDG_EUNSUPPORTED before touching a device."""
+    import ctypes as C
+    import paper_1601_07384_gb300 as g
+    from paper_1601_07384_gb300 import _lib
+    from inputs import kuhn_periodic_mesh
+    from oracle.mesh import Mesh as OMesh
+    v, t, per = kuhn_periodic_mesh(3)
+    gm = g.Mesh(v, t, period=per)
+    om = OMesh(v, t, period=per)
+    left, right, lf, rf = gm.faces()
+    assert gm.nf == om.nf == 2 * len(t) and gm.nboundary == 0
+    assert np.array_equal(left, om.left) and np.array_equal(right, om.right)
+    assert np.array_equal(lf, om.fl) and np.array_equal(rf, om.fr)
+    h = C.c_void_p()
+    st = _lib.load().stdg_solver_create(gm._h, g.Reference(1, 0)._h, 0.01, None, None, C.byref(h))
+    assert st == -8                                 # STDG_EUNSUPPORTED
+    with pytest.raises(g.StdgError):
+        g.Mesh(v, t, period=[0.0, 1.0, 1.0])
