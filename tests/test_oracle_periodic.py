@@ -111,3 +111,31 @@ def test_steady_abc_orders_p2():
     (v3, p3), (v4, p4) = errs
     ov, op = np.log(v3 / v4) / np.log(4 / 3), np.log(p3 / p4) / np.log(4 / 3)
     assert ov >= 2.3 and op >= 2.7, (errs, ov, op)
+
+
+def test_unsteady_abc_orders_p1_pt1():
+    """Unsteady ABC flow (nu = 1, p = p_t = 1, N_pic = 2, space-time pressure and implicit
+    viscosity) to t = 0.1 with dt = 0.1 / n on n = 3, 4: velocity order >= 1.7, pressure order
+    >= 1.4 (Table 2: 2.0 and 1.5-1.6; measured here 1.88 and 1.98, and 2.11 and 2.10 from n = 4
+    to 6)."""
+    nu = 1.0
+    errs = []
+    for n in (3, 4):
+        d = make(n, 1, 1, 0.1 / n)
+        st = initial_state(d, lambda x: abc_velocity(x, 0.0, nu))
+        for _ in range(n):
+            st = time_step(d, st, nu, 2, lambda x, t: abc_velocity(x, t, nu), method="direct")
+        vbar = ops.average(d, st.V)
+        ev, ws, pa, pb = 0.0, [], [], []
+        for i in range(d.mesh.ne):
+            x, w = map_tet(d.mesh.tet_coords(i), *d.tet_nl)
+            ph, _ = d.phi(i, x)
+            vh = np.stack([ph @ (d.g1 @ vbar[i, c].reshape(d.Ng, d.N)) for c in range(3)], 1)
+            ev += (w * ((vh - abc_velocity(x, st.t, nu)) ** 2).sum(1)).sum()
+            pa.append(ph @ (d.g1 @ st.P[i].reshape(d.Ng, d.N))); pb.append(abc_pressure(x, st.t, nu)); ws.append(w)
+        w, a, b = np.concatenate(ws), np.concatenate(pa), np.concatenate(pb)
+        a, b = a - (w * a).sum() / w.sum(), b - (w * b).sum() / w.sum()
+        errs.append((np.sqrt(ev), np.sqrt((w * (a - b) ** 2).sum())))
+    (v3, p3), (v4, p4) = errs
+    ov, op = np.log(v3 / v4) / np.log(4 / 3), np.log(p3 / p4) / np.log(4 / 3)
+    assert ov >= 1.7 and op >= 1.4, (errs, ov, op)
