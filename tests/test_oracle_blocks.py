@@ -236,7 +236,7 @@ def test_constant_mode_restriction():
     Galerkin restriction R (-A) R^T of the pinned pressure operator is the matrix of the (0, 0)
     entries of its blocks, and that matrix is symmetric positive definite."""
     from oracle.basis import dubiner
-    d = make(3, 2, 0, dt=0.01)
+    d = make(2, 2, 0, dt=0.01)
     xi = tet_rule(3)[0]
     phi, _ = dubiner(2, xi)
     assert np.abs(phi[:, 0] - phi[0, 0]).max() <= 1e-14 and np.abs(phi[:, 1:]).max() > 0.1
