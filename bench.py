@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the staggered space-time DG pressure-correction time step on one GB300.
 
-Workload (default): unit cube, 24^3 hexahedra x 6 = 82,944 jittered tetrahedra (seed 0),
-p = 3, p_t = 1 (N = 20, Nst = 40, 3,317,760 pressure DoFs), Beltrami data (a = pi/4,
-d = pi/2), nu = 0.01, dt = 0.005, 3 Picard iterations per step, pressure solves to a
-1e-10 relative residual.  A "step" is one full time step (stdg_step: averaging, convection,
-viscous solves, pressure right-hand side, pressure solve, velocity update, 3 times).
+Workload (default, "big"): unit cube, 40^3 hexahedra x 6 = 384,000 jittered tetrahedra (seed 0),
+p = 4, p_t = 4 (N = 35, Nst = 175, 67,200,000 pressure DoFs), initial velocity the seeded solenoidal
+field curl(b Psi) (64 Fourier modes drawn from splitmix64(seed 1), amplitude |k|^-3 in Psi, scaled
+to |v|max = 0.1) with no-slip walls, nu = 1e-3, dt = 0.01, 3 Picard iterations per step, pressure
+and viscous solves to a 1e-10 relative residual.  "mid": 24^3 x 6 = 82,944 tets, p = 3, p_t = 1,
+Beltrami data, nu = 0.01, dt = 0.005.  A "step" is one full time step (stdg_step: averaging,
+convection, viscous solves, pressure right-hand side, pressure solve, velocity update, n_picard times).
 
 Metric: seconds per time step with the chosen solver (Kronecker-decoupled block CG with the
-agglomeration coarse correction, mixed precision by default), next to plain FP64 GMRES(50); the
-dominant operator kernel's achieved throughput is reported as a roofline (HBM for binary32
-blocks, the FP64 pipe or the derived pair-arithmetic peak for the binary64-accurate kernels).
+agglomeration coarse correction, mixed precision by default), next to the plain FP64 solvers (the
+paper's GMRES(50), and unpreconditioned Kronecker CG); the dominant operator kernel's achieved
+throughput is reported as a roofline (HBM for binary32 blocks, the FP64 pipe or the derived
+pair-arithmetic peak for the binary64-accurate kernels).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload big|mid|...]
 """
 import argparse
 import json
@@ -29,13 +32,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s/time-step at 1e-10 residual (chosen vs plain FP64 GMRES); matvec HBM GB/s"
 WORKLOADS = {
-    "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
-    "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50),
-    "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
-    "learned": dict(n=6, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50),
-    "theta": dict(n=24, p=3, pt=0, nu=0.01, dt=0.005, npic=2, tol=1e-10, restart=50),
-    # the high-order degrees of the 40^3 configuration (p = p_t = 4, nu = 1e-3, dt = 0.01) on a 12^3 mesh
-    "hi": dict(n=12, p=4, pt=4, nu=1e-3, dt=0.01, npic=3, tol=1e-10, restart=50),
+    # the largest single-GPU configuration: p = p_t = 4 on 40^3 x 6 tets, solenoidal data, no-slip walls
+    "big": dict(n=40, p=4, pt=4, nu=1e-3, dt=0.01, npic=3, tol=1e-10, restart=50, data="solenoidal",
+                restart_every=0, gmres_cap=300, plain_cg_cap=1500, e2e_steps=2),
+    "mid": dict(n=24, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50, data="beltrami",
+                restart_every=6, gmres_cap=5000, plain_cg_cap=20000, e2e_steps=0),
+    "tiny": dict(n=3, p=1, pt=0, nu=0.1, dt=0.01, npic=2, tol=1e-12, restart=50, data="beltrami",
+                 restart_every=0, gmres_cap=5000, plain_cg_cap=20000, e2e_steps=0),
+    "prof": dict(n=16, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50, data="beltrami",
+                 restart_every=6, gmres_cap=5000, plain_cg_cap=20000, e2e_steps=0),
+    "learned": dict(n=6, p=3, pt=1, nu=0.01, dt=0.005, npic=3, tol=1e-10, restart=50, data="beltrami",
+                    restart_every=6, gmres_cap=5000, plain_cg_cap=20000, e2e_steps=0),
+    "theta": dict(n=24, p=3, pt=0, nu=0.01, dt=0.005, npic=2, tol=1e-10, restart=50, data="beltrami",
+                  restart_every=6, gmres_cap=5000, plain_cg_cap=20000, e2e_steps=0),
+    # the degrees of the largest configuration (p = p_t = 4, nu = 1e-3, dt = 0.01) on a 12^3 mesh
+    "hi": dict(n=12, p=4, pt=4, nu=1e-3, dt=0.01, npic=3, tol=1e-10, restart=50, data="solenoidal",
+               restart_every=0, gmres_cap=2000, plain_cg_cap=20000, e2e_steps=0),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 # binary64-accurate products from binary32 pairs: 12 FP32 lane operations per multiply-add term
@@ -43,7 +55,6 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk 
 DF_OPS_PER_TERM = 12
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / DF_OPS_PER_TERM * 2 / 1e12
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_operator_counts.json")
-RESTART = 6          # steps from the initial state before the run restarts from it (see advance())
 
 
 def nbasis(p):
@@ -53,8 +64,23 @@ def nbasis(p):
 def workload_name(w):
     ne = 6 * w["n"] ** 3
     N = nbasis(w["p"]); Nst = N * (w["pt"] + 1)
+    data = ("seeded solenoidal curl(b Psi) data (64 modes, |v|max 0.1), no-slip walls" if w["data"] == "solenoidal"
+            else "Beltrami data")
     return (f"Kuhn {w['n']}^3 hex x 6 = {ne:,} tets, p={w['p']}, p_t={w['pt']} ({ne * Nst:,} pressure DoFs), "
-            f"Beltrami data, nu={w['nu']}, dt={w['dt']}, {w['npic']} Picard iterations/step, tol {w['tol']:g}")
+            f"{data}, nu={w['nu']}, dt={w['dt']}, {w['npic']} Picard iterations/step, tol {w['tol']:g}")
+
+
+def set_data(solver, g, w):
+    """Initial and Dirichlet velocity of the workload (device field kinds)."""
+    if w["data"] == "solenoidal":
+        from inputs import SolenoidalModes
+        sm = SolenoidalModes(seed=1)
+        solver.set_initial(g.curl_modes(sm.k, sm.a, sm.phi, sm.scale))
+        solver.set_boundary(g.zero())
+    else:
+        fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
+        solver.set_initial(fld)
+        solver.set_boundary(fld)
 
 
 def mesh_counts(n):
@@ -127,9 +153,7 @@ class ClockSampler:
 
 def oracle_operator_sample(w, reps=3, n_sample=3):
     """The oracle's matrix-free pressure operator (as it stands) on a small mesh of the same
-    family, degrees and time step; returns seconds per application scaled to the full mesh
-    by the number of interior faces."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    family, degrees and time step: seconds per application on that mesh, and its interior faces."""
     from inputs import kuhn_mesh
     from oracle import operators as ops
     from oracle.blocks import SpaceTimeDG
@@ -144,9 +168,57 @@ def oracle_operator_sample(w, reps=3, n_sample=3):
         t0 = time.perf_counter()
         ops.pressure_apply(d, x)
         times.append(time.perf_counter() - t0)
-    nint_s = int(d.mesh.interior.sum())
-    _, nint, _ = mesh_counts(w["n"])
-    return float(np.median(times)) * nint / nint_s, nint_s
+    return float(np.median(times)), int(d.mesh.interior.sum())
+
+
+_ORACLE = {}
+
+
+def _oracle_init(w, n_sample):
+    """Pool initializer: the oracle's discretisation of the sample mesh, blocks precomputed (untimed)."""
+    from inputs import kuhn_mesh
+    from oracle.blocks import SpaceTimeDG
+    from oracle.mesh import Mesh
+    v, t = kuhn_mesh(n_sample, seed=0)
+    d = SpaceTimeDG(Mesh(v, t), w["p"], w["pt"], w["dt"])
+    for j in range(d.mesh.nf):
+        d.face_blocks(j)
+    _ORACLE["d"] = d
+    _ORACLE["x"] = np.random.default_rng(0).standard_normal((d.mesh.ne, d.Nst))
+
+
+def _oracle_apply(_):
+    from oracle import operators as ops
+    t0 = time.perf_counter()
+    ops.pressure_apply(_ORACLE["d"], _ORACLE["x"])
+    return time.perf_counter() - t0, int(_ORACLE["d"].mesh.interior.sum())
+
+
+class OracleOnHostCores:
+    """The oracle's operator sample run at once in one process per host core (spawned, one BLAS
+    thread each): every process applies the operator to its own copy of the sample mesh, so the
+    host's throughput is `cores` applications per per-process time.  sample() returns seconds per
+    application of the full mesh on all cores (extrapolated by interior faces), and the sample's
+    interior faces."""
+
+    def __init__(self, w, n_sample=3, cores=None):
+        import multiprocessing as mp
+        self.w = w
+        self.cores = cores or os.cpu_count() or 1
+        os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init, initargs=(w, n_sample))
+
+    def sample(self):
+        res = self.pool.map(_oracle_apply, range(self.cores), chunksize=1)
+        t_app = float(np.median([r[0] for r in res]))
+        nint_s = res[0][1]
+        _, nint, _ = mesh_counts(self.w["n"])
+        return t_app * nint / nint_s / self.cores, nint_s
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def operator_alone_ms(solver, lowprec, reps):
@@ -167,6 +239,7 @@ def operator_alone_ms(solver, lowprec, reps):
         run()
     e1.record(solver.stream)
     torch.cuda.synchronize()
+    del x, xf, y, yf
     return e0.elapsed_time(e1) / reps
 
 
@@ -183,42 +256,45 @@ def job_seconds_per_step(ms, steps, world, device="cuda"):
     return ms_max, ms_max / 1e3 / (steps * world)
 
 
-def cpu_threads():
-    try:
-        from threadpoolctl import threadpool_info
-        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-    except Exception:
-        n = 1
-    return 1 if os.environ.get("OMP_NUM_THREADS") == "1" else n
+def cpu_baseline_line(host, w, ops_per_step):
+    s_op, nint_s = host.sample()
+    cores = host.cores
+    return {"value": s_op * ops_per_step, "unit": "s/step", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": (f"extrapolated: the oracle's matrix-free pressure operator (FP64, as it stands) applied on "
+                       f"the {nint_s}-interior-face 3^3 mesh of the same family/p/p_t, once in each of {cores} "
+                       f"processes on {cores} host cores at once; per-application time scaled to "
+                       f"{mesh_counts(w['n'])[1]:,} interior faces, divided by {cores} cores, times "
+                       f"{ops_per_step:.0f} operator applications per step (the GPU arm's count); "
+                       f"the other per-step work is not included")}
 
 
 def reference_arm(args, w, world, rank):
     if rank != 0:
         return
-    counts = json.load(open(COUNTS_FILE)) if os.path.exists(COUNTS_FILE) else None
-    if counts is None or counts.get("workload") != workload_name(w):
+    counts = json.load(open(COUNTS_FILE)) if os.path.exists(COUNTS_FILE) else {}
+    entry = counts.get(workload_name(w)) if isinstance(counts, dict) else None
+    if entry is None:
         print(json.dumps({"impl": "reference", "unavailable": "no operator-application count recorded for this "
                           "workload (profiles/bench_operator_counts.json)"}))
         return
-    per_step_ops = counts["operator_applications_per_step"]
+    per_step_ops = entry["operator_applications_per_step"]
+    host = OracleOnHostCores(w)
     for _ in range(args.warmup):
-        oracle_operator_sample(w, reps=1)
+        host.sample()
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        s_op, nint_s = oracle_operator_sample(w, reps=1)
-        vals.append(s_op * per_step_ops)
+        line = cpu_baseline_line(host, w, per_step_ops)
+        vals.append(line["value"])
     wall = time.perf_counter() - t_all
+    host.close()
     v = float(np.median(vals))
-    sample = (f"oracle matrix-free pressure operator on the {nint_s}-interior-face 3^3 mesh of the same family/p/p_t, "
-              f"scaled to {mesh_counts(w['n'])[1]:,} interior faces x {per_step_ops} operator applications per step "
-              f"(count measured by the GPU arm on this workload); other per-step work not included")
+    line["value"] = v
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
                       "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": {"workload": workload_name(w), "parallelism": "replicas"},
-                      "cpu_baseline": {"value": v, "unit": "s/step", "cores": cpu_threads(), "kind": "oracle",
-                                       "sample": sample},
+                      "cpu_baseline": line,
                       "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                       "wall_s": wall}))
 
@@ -274,18 +350,24 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
-    ap.add_argument("--gmres-steps", type=int, default=1)
-    ap.add_argument("--gmres-max-iters", type=int, default=5000,
-                    help="iteration cap per pressure solve of the plain FP64 GMRES(50) comparison")
+    ap.add_argument("--workload", default="big", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end arm (0: the workload's default, else --steps)")
+    ap.add_argument("--gmres-max-iters", type=int, default=0,
+                    help="iteration cap per pressure solve of the plain FP64 GMRES(50) arm (0: workload default)")
+    ap.add_argument("--plain-cg-max-iters", type=int, default=0,
+                    help="iteration cap per pressure solve of the plain FP64 Kronecker CG arm (0: workload default)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 comparison arms (mixed vs FP64 step error, plain GMRES, plain CG)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--counts-out", default="",
-                    help="write this run's operator applications per step (JSON) to this path; "
-                         "profiles/bench_operator_counts.json is the copy the reference arm reads")
+                    help="merge this run's operator applications per step into this JSON file "
+                         "(profiles/bench_operator_counts.json is the copy the reference arm reads)")
     ap.add_argument("--precision", default="mixed_f32", choices=["fp64", "df32", "mixed_f32", "mixed_bf16"])
     ap.add_argument("--solver", default="kron_mg", choices=["kron_cg", "kron_pcg", "kron_mg", "gmres"])
     ap.add_argument("--theta", type=float, default=1.0,
                     help="semi-implicit pressure weight (p_t = 0 workloads only; 1 = fully implicit)")
+    ap.add_argument("--dt", type=float, default=0.0, help="override the workload's time step (labelled)")
     ap.add_argument("--learned", action="store_true",
                     help="learned-preconditioner protocol: harvest + train on early steps, evaluate FGMRES later")
     ap.add_argument("--graph-batch", type=int, default=8,
@@ -293,7 +375,9 @@ def main():
     ap.add_argument("--op-only", type=int, default=0,
                     help="only build the workload and apply the pressure operator this many times (profiling)")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.dt > 0:
+        w["dt"] = args.dt
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -315,31 +399,33 @@ def main():
 
     if args.learned:
         return learned_protocol(args, g, torch)
+    t_setup = time.perf_counter()
     v, t = kuhn_mesh(w["n"], seed=0)
     mesh = g.Mesh(v, t)
     ref = g.Reference(w["p"], w["pt"])
     solver = g.Solver(mesh, ref, w["dt"], precision=args.precision, restart=w["restart"], max_iters=200000,
                       graph_batch=args.graph_batch)
-    fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
     if args.op_only > 0:
         ms = operator_alone_ms(solver, args.precision.startswith("mixed"), args.op_only)
         print(json.dumps({"op_only": args.op_only, "precision": args.precision, "workload": workload_name(w),
                           "avg_launch_ms": ms}))
         return
-    solver.set_initial(fld)
-    solver.set_boundary(fld)
+    set_data(solver, g, w)
     if args.theta != 1.0:
         solver.set_theta(args.theta)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     stream = solver.stream
-    # At dt = 0.005 on this mesh (convective CFL of the DG scheme about 2) the time stepping is
-    # unstable: it stays bounded to t = 0.04 and diverges from step 9 on.  The configured dt is kept,
-    # and the run restarts from the initial state every RESTART steps (a device-to-device state
-    # copy, inside the timed region when it falls there), so any --steps/--warmup stay in range.
-    S0 = solver.get_state()
+    # At dt = 0.005 on the 24^3 mesh (convective CFL of the DG scheme about 2) the time stepping is
+    # unstable: it stays bounded to t = 0.04 and diverges from step 9 on.  There the configured dt is
+    # kept and the run restarts from the initial state every restart_every steps (a device-to-device
+    # state copy, inside the timed region when it falls there), so any --steps/--warmup stay in range.
+    every = w["restart_every"] if args.dt <= 0 else 0
+    S0 = solver.get_state() if every else None
     since = [0]
 
     def advance():
-        if since[0] == RESTART:
+        if every and since[0] == every:
             solver.set_state(*S0)
             since[0] = 0
         since[0] += 1
@@ -372,55 +458,26 @@ def main():
     ms, s_per_step = job_seconds_per_step(ms, args.steps, world)
 
     # ---- end to end through the C ABI with host buffers: every step copies its input state from
-    # pinned host memory and its result back; each repeats a timed step (same input state), so the
-    # run covers the same simulated interval as the timed region
+    # pinned host memory and its result back; each repeats the first timed step (same input state)
+    ne2e = args.e2e_steps or w["e2e_steps"] or args.steps
     P0, V0, t0 = solver.get_state()
     Pin = torch.empty(Pw.numel(), dtype=torch.float64).pin_memory(); Pin.copy_(Pw)
     Vin = torch.empty(Vw.numel(), dtype=torch.float64).pin_memory(); Vin.copy_(Vw)
     Ph = torch.empty(P0.numel(), dtype=torch.float64).pin_memory()
     Vh = torch.empty(V0.numel(), dtype=torch.float64).pin_memory()
+    del P0, V0
     lib = g._lib.load()
     import ctypes as C
     tcur = C.c_double(tw)
     barrier()
     te0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(ne2e):
         g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Pin.data_ptr()), C.c_void_p(Vin.data_ptr()), 0, tw))
         solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
         g._lib.check(lib.stdg_get_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0,
                                         C.byref(tcur)))
     barrier()
-    e2e = (time.perf_counter() - te0) / args.steps
-
-    # ---- the paper's plain FP64 solver on the same step (GMRES(50); CG when p_t = 0), same state
-    gm = None
-    if args.gmres_steps > 0:
-        solver.set_state(Pw, Vw, tw)
-        gsolver = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=args.gmres_max_iters)
-        gsolver.set_boundary(fld)
-        gsolver.set_state(Pw, Vw, tw)
-        if args.theta != 1.0:
-            gsolver.set_theta(args.theta)
-        plain = "cg" if w["pt"] == 0 else "gmres"      # the paper's solver: CG when p_t = 0
-        gts = []
-        ok = True
-        for _ in range(args.gmres_steps):
-            torch.cuda.synchronize()
-            tg0 = time.perf_counter()
-            try:
-                st = gsolver.step(w["nu"], w["npic"], method=plain, tol=w["tol"])
-            except g.StdgError as exc:
-                ok = False
-                st = {"error": str(exc)}
-            torch.cuda.synchronize()
-            gts.append(time.perf_counter() - tg0)
-        gm = {"method": plain, "s_per_step": float(np.median(gts)) if ok else None, "converged": ok,
-              "max_iters_per_solve": args.gmres_max_iters,
-              "press_iters": st.get("press_iters") if ok else None}
-        if not ok:      # the first pressure solve hit the cap: a lower bound on the plain solver's step
-            gm.update({"s_until_stopped": float(gts[-1]), "stopped": st["error"][:160],
-                       "s_per_step_lower_bound": float(gts[-1])})
-        del gsolver
+    e2e = (time.perf_counter() - te0) / ne2e
 
     # ---- roofline of the dominant operator kernel (CUDA-event time of its launches in the timed region)
     kinds = ["fp64 blocks (k_apply)", "binary32-pair blocks (k_apply_warp<WDF>)", "binary32 blocks (k_apply_warp<WF32>)",
@@ -439,9 +496,7 @@ def main():
     traffic = None
     tf = os.path.join(ROOT, "profiles", "operator_traffic.json")
     if os.path.exists(tf):
-        tr = json.load(open(tf))
-        key = f"{workload_name(w)}|{kinds[kbest]}"
-        traffic = tr.get(key)
+        traffic = json.load(open(tf)).get(f"{workload_name(w)}|{kinds[kbest]}")
     if kbest == 0:
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tflops / FP64_PEAK_TFLOPS,
@@ -453,13 +508,15 @@ def main():
                              f"{DF_OPS_PER_TERM} lane operations per multiply-add term x 2 flop"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "peak_note": f"HBM copy bandwidth, {hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+                "peak_note": f"HBM copy bandwidth, {hbm_src} (MEASURED_PEAKS.json hbm_gbs); of measured"}
     alone = operator_alone_ms(solver, kbest >= 2, 20)
     roof.update({"traffic": traffic, "kernel": kinds[kbest], "avg_launch_ms": op_launch_ms,
                  "alone_avg_launch_ms": alone,
                  "launches_timed": int(nlaunch_k), "algorithmic_bytes_per_launch": bytes_alg,
                  "flops_per_launch": flops, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                  "fp64_equiv_tflops": tflops})
+    mem = {"solver_device_bytes": solver.alloc_stats()[0], "max_allocated_bytes": torch.cuda.max_memory_allocated(),
+           "allocator": "PyTorch caching allocator (stdg_solver_create_alloc)"}
 
     out = {
         "metric": METRIC, "value": s_per_step * 1.0, "unit": "s/step", "n_gpus": world, "steps": args.steps,
@@ -467,18 +524,21 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "df32": "f64 (products from fp32 pairs)",
                                        "mixed_f32": "f64 outer (pair products) / f32 inner", "mixed_bf16": "f64 outer (pair products) / bf16 inner"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": workload_name(w) + (f", theta={args.theta}" if args.theta != 1.0 else ""),
-                   "steps": f"restarted from the initial state every {RESTART} steps (t <= {RESTART * w['dt']:g}): "
-                            f"at 24^3 tets, dt=0.005 the scheme diverges from step 9; restarts keep every timed step bounded",
+        "config": {"workload": workload_name(w) + (f", theta={args.theta}" if args.theta != 1.0 else "")
+                   + (f" (dt overridden to {w['dt']})" if args.dt > 0 else ""),
+                   "steps": (f"restarted from the initial state every {every} steps (t <= {every * w['dt']:g}): at "
+                             f"this dt the scheme diverges from step 9; restarts keep every timed step bounded")
+                   if every else "consecutive time steps",
                    "solver": args.solver, "precision": args.precision,
                    "parallelism": f"replicas only: {world} independent copies" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
         "roofline": roof,
-        "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(P0.numel() + V0.numel()) * 8,
-                "d2h_bytes_per_step": int(P0.numel() + V0.numel()) * 8},
+        "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(Pin.numel() + Vin.numel()) * 8,
+                "d2h_bytes_per_step": int(Ph.numel() + Vh.numel()) * 8, "steps": ne2e},
         "gpu_launches": int(prof["kernel_launches"]),
         "operator_applications_per_step": ops_per_step,
         "press_iters": [s["press_iters"] for s in stats],
+        "press_residual_max_per_step": [max(s["press_residual"]) for s in stats],
         "visc_iters": [s["visc_iters"] for s in stats],
         "max_divergence": max(s["max_divergence"] for s in stats),
         "matvecs_per_s": ops_per_step / (ms / 1e3 / args.steps),
@@ -491,21 +551,85 @@ def main():
                            "operator_kinds": {kinds[k]: {"launches_per_step": prof["kind_launches"][k] / args.steps,
                                                          "ms_per_launch": prof["kind_ms"][k] / max(prof["kind_launches"][k], 1)}
                                               for k in range(4) if prof["kind_launches"][k] > 0}},
-        "plain_gmres": gm,
+        "memory": mem,
+        "setup_s": setup_s,
         "clocks": clk.summary(),
     }
+    del solver
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # ---- FP64 comparison arms on a binary64 solver (created after the main one is freed: at the largest
+    # configuration two solvers do not fit side by side), all from the timed steps' starting state
+    if not args.no_compare:
+        gcap = args.gmres_max_iters or w["gmres_cap"]
+        ccap = args.plain_cg_max_iters or w["plain_cg_cap"]
+        f64 = g.Solver(mesh, ref, w["dt"], precision="fp64", restart=w["restart"], max_iters=200000)
+        set_data(f64, g, w)
+        if args.theta != 1.0:
+            f64.set_theta(args.theta)
+        cmp = {}
+
+        def run_step(method, cap):
+            f64.set_state(Pw, Vw, tw)
+            f64.set_max_iters(cap)
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            try:
+                st = f64.step(w["nu"], w["npic"], method=method, tol=w["tol"])
+                ok = True
+            except g.StdgError as exc:
+                st, ok = {"error": str(exc)[:200]}, False
+            torch.cuda.synchronize()
+            return st, ok, time.perf_counter() - a
+
+        if args.precision.startswith("mixed"):
+            # the mixed step's error against a binary64 step from the same state (same solver method)
+            st, ok, secs = run_step(args.solver, 200000)
+            P64, V64, _ = f64.get_state()
+            Pm, Vm = Ph.to("cuda"), Vh.to("cuda")
+            cmp["mixed_vs_fp64_step"] = {
+                "method": args.solver, "fp64_s_per_step": secs, "converged": ok,
+                "p_rel_l2": float(torch.linalg.norm(Pm - P64) / torch.linalg.norm(P64)),
+                "v_rel_l2": float(torch.linalg.norm(Vm - V64) / torch.linalg.norm(V64)),
+                "note": "one step from the timed steps' starting state; relative L2 norm of the coefficient vectors "
+                        "(orthonormal bases); the end-to-end arm's mixed result against the binary64 solver's"}
+            del Pm, Vm, P64, V64
+        # the paper's plain FP64 solver: GMRES(50) (CG when p_t = 0), capped: a lower bound if it stops
+        plain = "cg" if w["pt"] == 0 else "gmres"
+        st, ok, secs = run_step(plain, gcap)
+        cmp["plain_paper_solver"] = {"method": plain, "max_iters_per_solve": gcap, "converged": ok,
+                                     "s_per_step" if ok else "s_until_stopped": secs,
+                                     "press_iters": st.get("press_iters"), "stopped": st.get("error")}
+        if ok:
+            cmp["plain_paper_solver"]["press_residual_max"] = max(st["press_residual"])
+        # plain FP64 Kronecker CG (no preconditioner) on the same systems
+        if plain != "cg":
+            st, ok, secs = run_step("kron_cg", ccap)
+            cmp["plain_fp64_kron_cg"] = {"max_iters_per_solve": ccap, "converged": ok,
+                                         "s_per_step" if ok else "s_until_stopped": secs,
+                                         "press_iters": st.get("press_iters"), "stopped": st.get("error")}
+            if ok:
+                cmp["plain_fp64_kron_cg"]["press_residual_max"] = max(st["press_residual"])
+        out["fp64_comparisons"] = cmp
+        del f64
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     if rank == 0 and not args.no_cpu_baseline:
-        s_op, nint_s = oracle_operator_sample(w)
-        out["cpu_baseline"] = {
-            "value": s_op * ops_per_step, "unit": "s/step", "cores": cpu_threads(), "kind": "oracle",
-            "sample": (f"oracle matrix-free pressure operator on the {nint_s}-interior-face 3^3 mesh of the same "
-                       f"family/p/p_t, scaled to {mesh_counts(w['n'])[1]:,} interior faces x {ops_per_step:.0f} "
-                       f"operator applications per step; other per-step work not included")}
+        host = OracleOnHostCores(w)
+        out["cpu_baseline"] = cpu_baseline_line(host, w, ops_per_step)
+        host.close()
     if rank == 0:
         if args.counts_out:                      # the operator count the reference arm scales by
-            os.makedirs(os.path.dirname(os.path.abspath(args.counts_out)), exist_ok=True)
-            with open(args.counts_out, "w") as f:
-                json.dump({"workload": workload_name(w), "operator_applications_per_step": ops_per_step}, f)
+            path = os.path.abspath(args.counts_out)
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            cur = json.load(open(path)) if os.path.exists(path) else {}
+            if not isinstance(cur, dict) or "workload" in cur:
+                cur = {}
+            cur[workload_name(w)] = {"operator_applications_per_step": ops_per_step}
+            with open(path, "w") as f:
+                json.dump(cur, f, indent=1)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -129,13 +129,33 @@ typedef struct {
   int fallbacks;           /* pressure solves that fell back to plain GMRES               */
 } stdg_step_stats;
 
-/* Velocity data kinds for initial and Dirichlet boundary values (evaluated on the device).
+/* Velocity data kinds for initial and Dirichlet boundary values (evaluated on the device; the data
+ * of the problem statement, Sec. 2.4: initial velocity and prescribed boundary velocity).
  *  STDG_FIELD_ZERO     : v = 0 (no-slip walls).
  *  STDG_FIELD_CONSTANT : v = (c0, c1, c2).
  *  STDG_FIELD_BELTRAMI : Ethier-Steinman unsteady solution, params (a, d, nu):
- *      u = -a [e^{ax} sin(ay+dz) + e^{az} cos(ax+dy)] e^{-nu d^2 t}, v, w by cyclic shift. */
-enum { STDG_FIELD_ZERO = 0, STDG_FIELD_CONSTANT = 1, STDG_FIELD_BELTRAMI = 2 };
-typedef struct { int kind; double c[3]; double a, d, nu; } stdg_field;
+ *      u = -a [e^{ax} sin(ay+dz) + e^{az} cos(ax+dy)] e^{-nu d^2 t}, v, w by cyclic shift.
+ *  STDG_FIELD_CURL_MODES : the steady solenoidal field v = c0 curl(b Psi) of the unit cube, with
+ *      Psi(x) = Sum_m A_m sin(2 pi k_m . x + phi_m) and b = B^2, B = 64 x(1-x) y(1-y) z(1-z): b and
+ *      grad b vanish on the walls, so v = 0 there (no-slip compatible) and div v = 0 exactly.
+ *      `modes` points to nmodes host rows (k_m[3], A_m[3], phi_m) of 7 doubles (1 <= nmodes <= 256);
+ *      the call that receives the field copies them.
+ * Data that none of these kinds covers comes through a host callback (stdg_vel_fn below). */
+enum { STDG_FIELD_ZERO = 0, STDG_FIELD_CONSTANT = 1, STDG_FIELD_BELTRAMI = 2, STDG_FIELD_CURL_MODES = 3 };
+typedef struct { int kind; double c[3]; double a, d, nu; int nmodes; const double* modes; } stdg_field;
+
+/* Host velocity callback: fill uvw_host[n][3] with the velocity at the n space-time points
+ * xyzt_host[n][4] = (x, y, z, t).  Both arrays are host memory owned by the library and valid only
+ * during the call; `user` is passed through unchanged.  The callback must not call back into the
+ * library. */
+typedef void (*stdg_vel_fn)(const double* xyzt_host, int64_t n, double* uvw_host, void* user);
+
+/* Device allocator callbacks (stdg_solver_create_alloc): return `bytes` of device memory on the
+ * solver's device, usable on `stream` (the solver's stream), aligned to at least 256 bytes, or NULL
+ * on failure; free a pointer that alloc returned (with its size and the same stream).  Lets the
+ * caller's allocator own every device array of the solver, e.g. PyTorch's caching allocator. */
+typedef void* (*stdg_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*stdg_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 
 /* ---------------------------------------------------------------- mesh (Sec. 2.2) */
 /* Build the primary mesh and its face-based dual grid: faces from sorted vertex triples,
@@ -149,8 +169,9 @@ stdg_status stdg_mesh_create(const double* verts_host, int64_t nv, const int64_t
  * points of the box, tets_host index them (a vertex on a far face is the periodic image of one
  * on the near face), period_host[3] > 0 the box lengths.  A tet's geometry is its vertices'
  * periodic images nearest to its first vertex; faces are matched by vertex ids, so every face is
- * interior; face geometry is taken in l(j)'s frame.  Host-only.  A periodic mesh is not yet
- * accepted by stdg_solver_create (STDG_EUNSUPPORTED). */
+ * interior; face geometry is taken in l(j)'s frame, and every point of r(j) that meets face j (its
+ * barycentre, the quadrature points of T_{r,j}) is moved into that frame by a period vector.  Host-only;
+ * stdg_solver_create accepts the result like any mesh (no boundary faces: no Dirichlet data). */
 stdg_status stdg_mesh_create_periodic(const double* verts_host, int64_t nv, const int64_t* tets_host,
                                       int64_t ne, const double* period_host, stdg_mesh** out);
 void stdg_mesh_destroy(stdg_mesh* mesh);
@@ -221,9 +242,21 @@ typedef struct {
 stdg_status stdg_solver_create(const stdg_mesh* mesh, const stdg_ref* ref, double dt,
                                const stdg_solver_options* opts, void* cuda_stream,
                                stdg_solver** out);
+/* The same, with every device array of the solver (blocks, state, Krylov and step workspace, the
+ * lazily built copies and hierarchies) obtained from alloc_fn(bytes, cuda_stream, user) and returned
+ * through free_fn by stdg_solver_destroy, after the solver's stream has been synchronised.  alloc_fn
+ * and free_fn must both be given (else STDG_EINVAL); a NULL return from alloc_fn is STDG_ENOMEM.
+ * Allocation happens in this call and lazily in the first call that needs an array (stdg_step,
+ * stdg_solve, ...), never during the library's own CUDA-graph captures.  Host pinned buffers, CUDA
+ * events and graphs stay with the CUDA runtime; stdg_solve_noalloc never allocates. */
+stdg_status stdg_solver_create_alloc(const stdg_mesh* mesh, const stdg_ref* ref, double dt,
+                                     const stdg_solver_options* opts, void* cuda_stream, stdg_alloc_fn alloc_fn,
+                                     stdg_free_fn free_fn, void* user, stdg_solver** out);
 void stdg_solver_destroy(stdg_solver* s);
 /* Change the time step (rebuilds only the Ng x Ng time factor dt^2 K^-1). */
 stdg_status stdg_set_dt(stdg_solver* s, double dt);
+/* Change the cap on Krylov iterations per solve (stdg_solver_options.max_iters); STDG_EINVAL if < 1. */
+stdg_status stdg_set_max_iters(stdg_solver* s, int max_iters);
 
 /* ---------------------------------------------------------------- hot-path kernels */
 /* y = A x, the five-point block pressure operator of Eq. CS_19 / A2_mod (left-hand side):
@@ -281,7 +314,12 @@ stdg_status stdg_solve(stdg_solver* s, const double* b_dev, double* x_dev, doubl
  *  - All calls share the one array, which keeps whatever the last call left in it (x is set to
  *    zero before the iteration; everything else is written before it is read).  Calls whose
  *    device work overlaps -- on different streams or from different threads -- race on it.
- *  - b_dev, x_dev, tol, stats and the result are as for stdg_solve with STDG_SOLVER_KRON_CG. */
+ *  - It always runs the Kronecker-decoupled CG on the binary64-accurate operator (binary64 blocks,
+ *    or their binary32-pair form when the solver was created with another precision option), one
+ *    host check per iteration: never the mixed-precision inner-outer iteration that stdg_solve runs
+ *    for STDG_SOLVER_KRON_CG under STDG_PREC_MIXED_*.  Its iterates then differ from that call's at
+ *    rounding level and its iteration count from that call's.
+ *  - b_dev, x_dev, tol and stats are as for stdg_solve; a non-finite b is STDG_ENAN. */
 stdg_status stdg_solve_noalloc(stdg_solver* s, const double* b_dev, double* x_dev, double tol,
                                stdg_solve_stats* stats);
 
@@ -291,6 +329,22 @@ stdg_status stdg_solve_noalloc(stdg_solver* s, const double* b_dev, double* x_de
 stdg_status stdg_set_initial(stdg_solver* s, const stdg_field* field);
 /* Dirichlet velocity on the boundary (all boundary faces), evaluated each step. */
 stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* field);
+/* The same two, with the data from a host callback instead of a device field kind (the problem
+ * statement of Sec. 2.4 allows any initial and boundary velocity).  The library computes the
+ * quadrature points on the device with the kernels that consume the values, copies them to the host
+ * and calls fn on them:
+ *  - stdg_set_initial_fn calls fn once, at t = 0, with nf * 2 * nq points (nq: the nonlinear-degree
+ *    tetrahedron rule, ceil((3p+2)/2)^3 points per sub-tetrahedron; unused slots of boundary faces
+ *    carry the point (0, 0, 0, 0)), then projects as stdg_set_initial does.  Host and device memory
+ *    of the call scale with nf * nq: meant for meshes up to ~10^5 faces; use a device kind beyond.
+ *  - stdg_set_boundary_fn collects the space-time points of every boundary dual cell and boundary
+ *    face once (nboundary * (nq + nqf) * nt points: sub-tetrahedron and face rules of the nonlinear
+ *    degree times the time rule) and calls fn at the start of every stdg_step, t = t^n + tau dt.
+ *    The same values serve the boundary projections (readings R2, R25) and the boundary flux of the
+ *    convection (Eq. convdg, v+ = v_bc).
+ * STDG_EINVAL on a NULL fn; a later stdg_set_boundary replaces the callback. */
+stdg_status stdg_set_initial_fn(stdg_solver* s, stdg_vel_fn fn, void* user);
+stdg_status stdg_set_boundary_fn(stdg_solver* s, stdg_vel_fn fn, void* user);
 /* One time step t -> t + dt of the Picard pressure-correction algorithm (Sec. 2.6, steps
  * 0-6), n_picard Picard iterations, viscosity nu; pressure solves with `method` to `tol`,
  * viscous solves (Eq. A1_mod) to `tol`: decoupled in time with K = W R W^-1

@@ -10,9 +10,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import FIELD, PREC, SOLVER, Field, SolveStats, SolverOptions, StdgError, StepStats
+from ._lib import ALLOC_FN, FIELD, FREE_FN, PREC, SOLVER, VEL_FN, Field, SolveStats, SolverOptions, StdgError, StepStats
 
-__all__ = ["Mesh", "Reference", "Solver", "StdgError", "beltrami", "constant", "zero", "nbasis", "time_blockdiag"]
+__all__ = ["Mesh", "Reference", "Solver", "StdgError", "beltrami", "constant", "zero", "curl_modes", "nbasis",
+           "time_blockdiag"]
 
 
 def nbasis(p):
@@ -42,6 +43,20 @@ def constant(u):
 
 def zero():
     f = Field(); f.kind = FIELD["zero"]
+    return f
+
+
+def curl_modes(k, A, phi, scale=1.0):
+    """STDG_FIELD_CURL_MODES: v = scale curl(b Psi), Psi = Sum_m A_m sin(2 pi k_m . x + phi_m),
+    b = (64 x(1-x) y(1-y) z(1-z))^2 on the unit cube (zero with its gradient on the walls)."""
+    k = np.asarray(k, dtype=np.float64).reshape(-1, 3)
+    A = np.asarray(A, dtype=np.float64).reshape(-1, 3)
+    phi = np.asarray(phi, dtype=np.float64).reshape(-1, 1)
+    rows = np.ascontiguousarray(np.concatenate([k, A, phi], axis=1))
+    f = Field(); f.kind = FIELD["curl_modes"]; f.c[0] = float(scale)
+    f.nmodes = rows.shape[0]
+    f.modes = rows.ctypes.data_as(_lib.DP)
+    f._rows = rows                      # keeps the host table alive while the Field is
     return f
 
 
@@ -145,22 +160,79 @@ def tet_rule(n):
 
 
 class Solver:
-    """Device-resident discretisation: blocks, state and Krylov workspace (stdg_solver_create)."""
+    """Device-resident discretisation: blocks, state and Krylov workspace (stdg_solver_create).
+
+    allocator="torch" (default): every device array of the solver comes from PyTorch's caching
+    allocator (stdg_solver_create_alloc with callbacks into torch.cuda.caching_allocator_alloc /
+    caching_allocator_delete); allocator="cuda": the library calls cudaMalloc itself.  The callbacks
+    count what they hand out: alloc_stats() gives the live bytes and the allocation count."""
 
     def __init__(self, mesh: Mesh, ref: Reference, dt, precision="fp64", restart=50, max_iters=200000,
-                 stream=None, graph_batch=8):
+                 stream=None, graph_batch=8, allocator="torch"):
         torch = _torch()
         lib = _lib.load()
         self.mesh, self.ref = mesh, ref
         self.N, self.Ng, self.Nst = ref.N, ref.Ng, ref.Nst
         self.ne, self.nf = mesh.ne, mesh.nf
         self.dt = float(dt)
+        self._cb_error = None
+        self._live = {}
+        self._nalloc = [0]
         opts = SolverOptions(PREC[precision], int(restart), int(max_iters), int(graph_batch))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        _lib.check(lib.stdg_solver_create(mesh._h, ref._h, self.dt, C.byref(opts),
-                                          C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        if allocator == "torch":
+            dev = torch.cuda.current_device()
+            live, count = self._live, self._nalloc          # no reference to self: no cycle
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    p = torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=int(stream or 0))
+                except Exception:                       # the library reports STDG_ENOMEM
+                    return None
+                live[int(p)] = int(nbytes)
+                count[0] += 1
+                return p
+
+            def _free(ptr, nbytes, stream, user):
+                try:
+                    live.pop(int(ptr), None)
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:                       # interpreter shutdown: torch may be gone
+                    pass
+
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+            _lib.check(lib.stdg_solver_create_alloc(mesh._h, ref._h, self.dt, C.byref(opts),
+                                                    C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
+                                                    self._free_cb, None, C.byref(h)))
+        elif allocator == "cuda":
+            _lib.check(lib.stdg_solver_create(mesh._h, ref._h, self.dt, C.byref(opts),
+                                              C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        else:
+            raise ValueError(f"allocator must be 'torch' or 'cuda', not {allocator!r}")
         self._h = h
+
+    def alloc_stats(self):
+        """(live bytes, allocations so far) handed out through the allocator callbacks."""
+        return sum(self._live.values()), self._nalloc[0]
+
+    def _vel_callback(self, fn):
+        """stdg_vel_fn around fn(x (n, 3), t (n,)) -> (n, 3); an exception is re-raised after the call."""
+        def cb(xyzt, n, uvw, user):
+            out = np.ctypeslib.as_array(uvw, shape=(n, 3))
+            try:
+                X = np.ctypeslib.as_array(xyzt, shape=(n, 4))
+                out[:] = np.asarray(fn(X[:, :3].copy(), X[:, 3].copy()), dtype=np.float64).reshape(n, 3)
+            except BaseException as exc:                # surfaced by _check_cb
+                self._cb_error = exc
+                out[:] = np.nan
+        return VEL_FN(cb)
+
+    def _check_cb(self, status):
+        err, self._cb_error = self._cb_error, None
+        if err is not None:
+            raise err
+        _lib.check(status)
 
     # ---------------------------------------------------------------- helpers
     def pressure_empty(self):
@@ -181,6 +253,9 @@ class Solver:
     def set_dt(self, dt):
         self.dt = float(dt)
         _lib.check(_lib.load().stdg_set_dt(self._h, self.dt))
+
+    def set_max_iters(self, n):
+        _lib.check(_lib.load().stdg_set_max_iters(self._h, int(n)))
 
     def pressure_apply(self, x, y=None, pinned=True):
         x = self._dev(x)
@@ -240,14 +315,28 @@ class Solver:
 
     # ---------------------------------------------------------------- time stepping
     def set_initial(self, field):
-        _lib.check(_lib.load().stdg_set_initial(self._h, C.byref(field)))
+        """Initial velocity: a device field kind (Field), or a host callable fn(x (n, 3), t (n,)) -> (n, 3)
+        evaluated at the projection's quadrature points (stdg_set_initial_fn)."""
+        if callable(field):
+            cb = self._vel_callback(field)
+            self._check_cb(_lib.load().stdg_set_initial_fn(self._h, cb, None))
+        else:
+            _lib.check(_lib.load().stdg_set_initial(self._h, C.byref(field)))
 
     def set_boundary(self, field):
-        _lib.check(_lib.load().stdg_set_boundary(self._h, C.byref(field)))
+        """Dirichlet velocity: a device field kind, or a host callable evaluated at every step's boundary
+        quadrature points (stdg_set_boundary_fn)."""
+        if callable(field):
+            self._bc_cb = self._vel_callback(field)          # called from every stdg_step
+            self._check_cb(_lib.load().stdg_set_boundary_fn(self._h, self._bc_cb, None))
+        else:
+            _lib.check(_lib.load().stdg_set_boundary(self._h, C.byref(field)))
+            self._bc_cb = None
 
     def step(self, nu, n_picard, method="kron_cg", tol=1e-10):
         st = StepStats()
-        _lib.check(_lib.load().stdg_step(self._h, float(nu), int(n_picard), SOLVER[method], float(tol), C.byref(st)))
+        self._check_cb(_lib.load().stdg_step(self._h, float(nu), int(n_picard), SOLVER[method], float(tol),
+                                             C.byref(st)))
         k = st.picard
         return {"picard": k, "press_iters": list(st.press_iters[:k]), "visc_iters": list(st.visc_iters[:k]),
                 "press_residual": list(st.press_residual[:k]), "seconds": st.seconds,

@@ -9,7 +9,7 @@ STATUS = {0: "STDG_OK", -1: "STDG_EINVAL", -2: "STDG_ENOMEM", -3: "STDG_ECUDA", 
           -5: "STDG_EMESH", -6: "STDG_ENAN", -7: "STDG_ETIMEOUT", -8: "STDG_EUNSUPPORTED"}
 SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5, "kron_mg": 6}
 PREC = {"fp64": 0, "df32": 1, "mixed_f32": 2, "mixed_bf16": 3}
-FIELD = {"zero": 0, "constant": 1, "beltrami": 2}
+FIELD = {"zero": 0, "constant": 1, "beltrami": 2, "curl_modes": 3}
 
 
 class StdgError(RuntimeError):
@@ -40,7 +40,13 @@ class ProfileStats(C.Structure):
 
 class Field(C.Structure):
     _fields_ = [("kind", C.c_int), ("c", C.c_double * 3), ("a", C.c_double), ("d", C.c_double),
-                ("nu", C.c_double)]
+                ("nu", C.c_double), ("nmodes", C.c_int), ("modes", C.POINTER(C.c_double))]
+
+
+# stdg_vel_fn, stdg_alloc_fn, stdg_free_fn
+VEL_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_void_p)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 
 P = C.c_void_p
@@ -64,8 +70,11 @@ SIGNATURES = {
     "stdg_ref_eval": (C.c_int, [P, DP, C.c_int64, DP, DP]),
     "stdg_tet_rule": (C.c_int, [C.c_int, DP, DP]),
     "stdg_solver_create": (C.c_int, [P, P, C.c_double, C.POINTER(SolverOptions), P, C.POINTER(P)]),
+    "stdg_solver_create_alloc": (C.c_int, [P, P, C.c_double, C.POINTER(SolverOptions), P, ALLOC_FN, FREE_FN, P,
+                                           C.POINTER(P)]),
     "stdg_solver_destroy": (None, [P]),
     "stdg_set_dt": (C.c_int, [P, C.c_double]),
+    "stdg_set_max_iters": (C.c_int, [P, C.c_int]),
     "stdg_pressure_apply": (C.c_int, [P, P, P, C.c_int]),
     "stdg_pressure_apply_f32": (C.c_int, [P, P, P, C.c_int]),
     "stdg_pressure_apply_factored": (C.c_int, [P, P, P, C.c_int]),
@@ -75,6 +84,8 @@ SIGNATURES = {
     "stdg_solve_noalloc": (C.c_int, [P, P, P, C.c_double, C.POINTER(SolveStats)]),
     "stdg_set_initial": (C.c_int, [P, C.POINTER(Field)]),
     "stdg_set_boundary": (C.c_int, [P, C.POINTER(Field)]),
+    "stdg_set_initial_fn": (C.c_int, [P, VEL_FN, P]),
+    "stdg_set_boundary_fn": (C.c_int, [P, VEL_FN, P]),
     "stdg_step": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.POINTER(StepStats)]),
     "stdg_set_theta": (C.c_int, [P, C.c_double]),
     "stdg_get_state": (C.c_int, [P, P, P, C.c_int, DP]),

@@ -50,14 +50,11 @@ stdg_status check(stdg_solver* s) {
 
 }  // namespace
 
-extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r, double dt,
-                                          const stdg_solver_options* opts, void* stream, stdg_solver** out) {
+static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double dt, const stdg_solver_options* opts,
+                                 void* stream, stdg_alloc_fn alloc_fn, stdg_free_fn free_fn, void* user,
+                                 stdg_solver** out) {
   if (!m || !r || !out || !(dt > 0.0)) { set_error("stdg_solver_create: invalid argument"); return STDG_EINVAL; }
   *out = nullptr;
-  if (m->periodic) {                      // the device kernels map points without periodic images
-    set_error("stdg_solver_create: periodic meshes are supported by the host mesh only (not yet by the solver)");
-    return STDG_EUNSUPPORTED;
-  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     set_error("stdg_solver_create: no CUDA device available (this library has no CPU path)");
@@ -68,6 +65,7 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   if (!s) { set_error("out of host memory"); return STDG_ENOMEM; }
   cudaGetDevice(&s->device);
   s->stream = (cudaStream_t)stream;
+  s->alloc_fn = alloc_fn; s->free_fn = free_fn; s->alloc_user = user;
   s->opt.precision = STDG_PREC_FP64; s->opt.restart = 50; s->opt.max_iters = 200000; s->opt.graph_batch = 8;
   if (opts) {
     s->opt = *opts;
@@ -118,6 +116,11 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
       }
     TRY(upload(s, &s->gface, gf.data(), gf.size()));
     TRY(upload(s, &s->gnbr, gn.data(), gn.size()));
+    // compact boundary index of every face (-1: interior), for data given at boundary points
+    std::vector<int> bi(m->nf);
+    int nb = 0;
+    for (int64_t j = 0; j < m->nf; ++j) bi[j] = m->right[j] < 0 ? nb++ : -1;
+    TRY(upload(s, &s->bidx, bi.data(), bi.size()));
   }
   std::vector<double> X0(3 * m->ne), fvx(9 * m->nf);
   for (int64_t i = 0; i < m->ne; ++i)
@@ -133,6 +136,7 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   TRY(upload(s, &d.fvx, fvx.data(), fvx.size()));
   TRY(upload(s, &d.normal, m->normal.data(), m->normal.size()));
   TRY(upload(s, &d.area, m->area.data(), m->area.size()));
+  TRY(upload(s, &d.fshift, m->fshift.data(), m->fshift.size()));
   // reference tables
   DevRef& t = s->dr;
   TRY(upload(s, &t.sub_lin_xi, r->sub_lin_xi.data(), r->sub_lin_xi.size()));
@@ -190,6 +194,18 @@ extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r,
   return STDG_OK;
 }
 
+extern "C" stdg_status stdg_solver_create(const stdg_mesh* m, const stdg_ref* r, double dt,
+                                          const stdg_solver_options* opts, void* stream, stdg_solver** out) {
+  return solver_create(m, r, dt, opts, stream, nullptr, nullptr, nullptr, out);
+}
+
+extern "C" stdg_status stdg_solver_create_alloc(const stdg_mesh* m, const stdg_ref* r, double dt,
+                                                const stdg_solver_options* opts, void* stream, stdg_alloc_fn alloc_fn,
+                                                stdg_free_fn free_fn, void* user, stdg_solver** out) {
+  if (!alloc_fn || !free_fn) { set_error("stdg_solver_create_alloc: alloc_fn and free_fn are both needed"); return STDG_EINVAL; }
+  return solver_create(m, r, dt, opts, stream, alloc_fn, free_fn, user, out);
+}
+
 extern "C" void stdg_solver_destroy(stdg_solver* s) {
   if (!s) return;
   cudaSetDevice(s->device);
@@ -198,7 +214,11 @@ extern "C" void stdg_solver_destroy(stdg_solver* s) {
   for (cudaEvent_t e : s->gev) cudaEventDestroy(e);
   for (cudaEvent_t e : s->sync_ev) if (e) cudaEventDestroy(e);
   if (s->cstream) cudaStreamDestroy(s->cstream);
-  for (void* p : s->allocs) cudaFree(p);
+  for (size_t k = s->allocs.size(); k-- > 0;) {
+    if (s->free_fn) s->free_fn(s->allocs[k].p, s->allocs[k].bytes, (void*)s->stream, s->alloc_user);
+    else cudaFree(s->allocs[k].p);
+  }
+  s->allocs.clear();
   if (s->hostbuf) cudaFreeHost(s->hostbuf);
   mg_free(s);
   delete s->gnn;
@@ -211,6 +231,14 @@ extern "C" stdg_status stdg_set_dt(stdg_solver* s, double dt) {
   if (!(dt > 0.0)) { set_error("dt must be positive"); return STDG_EINVAL; }
   s->dt = dt;
   set_time_mats(s);
+  return STDG_OK;
+}
+
+extern "C" stdg_status stdg_set_max_iters(stdg_solver* s, int max_iters) {
+  stdg_status e = check(s);
+  if (e != STDG_OK) return e;
+  if (max_iters < 1) { set_error("max_iters must be >= 1"); return STDG_EINVAL; }
+  s->opt.max_iters = max_iters;
   return STDG_OK;
 }
 

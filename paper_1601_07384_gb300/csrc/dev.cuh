@@ -42,6 +42,7 @@ struct DevMesh {
   int *t2f = nullptr, *t2n = nullptr, *t2code = nullptr;
   double *X0 = nullptr, *J = nullptr, *Jinv = nullptr, *detJ = nullptr, *bary = nullptr;
   double *fvx = nullptr, *normal = nullptr, *area = nullptr;
+  double* fshift = nullptr;   // [nf][3]: r(j)'s frame -> l(j)'s frame (a period vector on periodic meshes)
 };
 
 // Device copies of the reference tables (layouts as in stdg_ref).
@@ -104,10 +105,19 @@ cudaError_t launch_moments(int nf, int N, int Ng, const double* Mij, const doubl
 }  // namespace stdg
 
 namespace stdg {
-// Velocity data evaluated on the device (stdg_field).
-struct FieldArg { int kind; double c[3]; double a, d, nu; };
+// Velocity data evaluated on the device (stdg_field), plus two internal kinds for data from a host
+// callback: kFieldTable reads the value the callback returned for point `pid`; kFieldCollect records
+// the point (x, y, z, tau) at `pid` so that the host can evaluate the callback there, and yields 0.
+constexpr int kFieldTable = 100;
+constexpr int kFieldCollect = 101;
+struct FieldArg {
+  int kind; double c[3]; double a, d, nu;
+  int nmodes; const double* modes;   // STDG_FIELD_CURL_MODES: per mode k (3), A (3), phi, 2 pi k x A (3)
+  const double* table;               // kFieldTable: [pid][3]
+  double* collect;                   // kFieldCollect: [pid][4]
+};
 
-__device__ inline void eval_field(const FieldArg& f, const double* x, double t, double* v) {
+__device__ inline void eval_field(const FieldArg& f, const double* x, double t, int64_t pid, double tau, double* v) {
   if (f.kind == STDG_FIELD_CONSTANT) { v[0] = f.c[0]; v[1] = f.c[1]; v[2] = f.c[2]; return; }
   if (f.kind == STDG_FIELD_BELTRAMI) {
     const double a = f.a, d = f.d, X = x[0], Y = x[1], Z = x[2];
@@ -116,6 +126,37 @@ __device__ inline void eval_field(const FieldArg& f, const double* x, double t, 
     v[1] = -a * (exp(a * Y) * sin(a * Z + d * X) + exp(a * X) * cos(a * Y + d * Z)) * e;
     v[2] = -a * (exp(a * Z) * sin(a * X + d * Y) + exp(a * Y) * cos(a * Z + d * X)) * e;
     return;
+  }
+  if (f.kind == STDG_FIELD_CURL_MODES) {
+    // v = c0 curl(b Psi) = c0 (grad b x Psi + b curl Psi), b = B^2, B = 64 x(1-x) y(1-y) z(1-z)
+    const double X = x[0], Y = x[1], Z = x[2];
+    const double px = X * (1.0 - X), py = Y * (1.0 - Y), pz = Z * (1.0 - Z);
+    const double B = 64.0 * px * py * pz;
+    const double g0 = 2.0 * B * 64.0 * (1.0 - 2.0 * X) * py * pz;
+    const double g1 = 2.0 * B * 64.0 * px * (1.0 - 2.0 * Y) * pz;
+    const double g2 = 2.0 * B * 64.0 * px * py * (1.0 - 2.0 * Z);
+    const double b = B * B;
+    double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0, cu0 = 0.0, cu1 = 0.0, cu2 = 0.0;
+    for (int m = 0; m < f.nmodes; ++m) {
+      const double* md = f.modes + 10 * m;
+      const double th = 2.0 * 3.14159265358979323846 * (md[0] * X + md[1] * Y + md[2] * Z) + md[6];
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      ps0 = fma(md[3], sn, ps0); ps1 = fma(md[4], sn, ps1); ps2 = fma(md[5], sn, ps2);
+      cu0 = fma(md[7], cs, cu0); cu1 = fma(md[8], cs, cu1); cu2 = fma(md[9], cs, cu2);
+    }
+    v[0] = f.c[0] * (g1 * ps2 - g2 * ps1 + b * cu0);
+    v[1] = f.c[0] * (g2 * ps0 - g0 * ps2 + b * cu1);
+    v[2] = f.c[0] * (g0 * ps1 - g1 * ps0 + b * cu2);
+    return;
+  }
+  if (f.kind == kFieldTable) {
+    v[0] = f.table[3 * pid]; v[1] = f.table[3 * pid + 1]; v[2] = f.table[3 * pid + 2];
+    return;
+  }
+  if (f.kind == kFieldCollect) {
+    f.collect[4 * pid] = x[0]; f.collect[4 * pid + 1] = x[1]; f.collect[4 * pid + 2] = x[2];
+    f.collect[4 * pid + 3] = tau;
   }
   v[0] = v[1] = v[2] = 0.0;
 }

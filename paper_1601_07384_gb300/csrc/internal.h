@@ -52,6 +52,8 @@ struct stdg_mesh {
   bool periodic = false;                 // periodic box: vertex ids are lattice points of the box
   double period[3] = {0, 0, 0};
   std::vector<double> fcoords;           // nf*9: canonical face vertex coordinates in l(j)'s frame
+  std::vector<double> fshift;            // nf*3: a point of r(j) in l(j)'s frame = in r(j)'s frame + fshift
+                                         //       (a period vector on a periodic mesh, else 0)
 };
 
 struct stdg_ref {

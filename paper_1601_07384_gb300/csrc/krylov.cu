@@ -448,14 +448,43 @@ __global__ void k_scale_copy(int64_t n, const double* __restrict__ in, const dou
     out[e] = (mode == 0) ? in[e] * f : in[e] - out[e];
 }
 
+// Every device array of a solver comes from here: the caller's allocator when one was given at
+// creation, else cudaMalloc.  The arrays are released together by stdg_solver_destroy.
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-  if (e != cudaSuccess) {
-    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    return STDG_ENOMEM;
+  const size_t b = bytes ? bytes : 16;
+  *p = nullptr;
+  if (s->alloc_fn) {
+    *p = s->alloc_fn(b, (void*)s->stream, s->alloc_user);
+    if (!*p) {
+      set_error("device allocation of %zu bytes failed (caller's allocator)", b);
+      return STDG_ENOMEM;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(p, b);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      set_error("cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+      return STDG_ENOMEM;
+    }
   }
-  s->allocs.push_back(*p);
+  s->allocs.push_back({*p, b});
   return STDG_OK;
+}
+
+cudaError_t dev_alloc_cuda(stdg_solver* s, void** p, size_t bytes) {
+  return dev_alloc(s, p, bytes) == STDG_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+// Release one array obtained from dev_alloc before the solver is destroyed (stream-ordered use of it
+// must have finished: the caller synchronises first).
+void dev_free(stdg_solver* s, void* p) {
+  for (size_t k = 0; k < s->allocs.size(); ++k)
+    if (s->allocs[k].p == p) {
+      if (s->free_fn) s->free_fn(p, s->allocs[k].bytes, (void*)s->stream, s->alloc_user);
+      else cudaFree(p);
+      s->allocs.erase(s->allocs.begin() + (long)k);
+      return;
+    }
 }
 
 stdg_status ensure_krylov(stdg_solver* s) {
@@ -1202,6 +1231,7 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
   }
   const int64_t n = s->ne * (int64_t)s->Nst;
   const double bn = host_norm(s, b, n);
+  if (!std::isfinite(bn)) { set_error("stdg_solve: non-finite right-hand side"); return STDG_ENAN; }
   int it = 0, rs = 0;
   double rabs = 0.0;
   stdg_status r = STDG_OK;
@@ -1595,6 +1625,7 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
   for (int q = 0; q < s->Ng * s->Ng; ++q) a.Kmass[q] = s->K[q];
   const int64_t n = s->ne * (int64_t)s->Nst;
   const double bn = host_norm(s, b, n);
+  if (!std::isfinite(bn)) { set_error("viscous solve: non-finite right-hand side"); return STDG_ENAN; }
   if (bn == 0.0) { cudaMemsetAsync(x, 0, n * sizeof(double), s->stream); *iters = 0; *res = 0; return STDG_OK; }
   int rs = 0;
   // Decoupled COCG (above); then GMRES from its result, which only checks the true residual of the
@@ -1722,6 +1753,7 @@ stdg_status solve_pressure_noalloc(stdg_solver* s, const double* b, double* x, d
   double* rrnew = scal + 32; double* res = scal + 48; double* nrm = scal + 56;
   double bn = 0.0;
   if ((e = noalloc_norm(s, b, n, part, nrm, &bn)) != STDG_OK) return e;
+  if (!std::isfinite(bn)) { set_error("stdg_solve_noalloc: non-finite right-hand side"); return STDG_ENAN; }
   // x starts at zero; every other scratch value is written before it is read
   cudaMemsetAsync(x, 0, n * sizeof(double), s->stream);
   int it = 0;

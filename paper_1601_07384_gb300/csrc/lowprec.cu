@@ -323,13 +323,13 @@ __global__ void k_to_lp<__nv_bfloat16>(int64_t nblk, int NN, int SB, const doubl
 }
 
 template <typename TB>
-static cudaError_t build_lp(int64_t ne, int64_t nf, int N, const double* Bdiag, const double* Aoff, void** Bd, void** Ao,
-                            int* SB, cudaStream_t st) {
+static cudaError_t build_lp(stdg_solver* s, int64_t ne, int64_t nf, int N, const double* Bdiag, const double* Aoff,
+                            void** Bd, void** Ao, int* SB, cudaStream_t st) {
   const int align = 16 / (int)sizeof(TB);
   const int sb = ((N * N + align - 1) / align) * align;
-  cudaError_t e = cudaMalloc(Bd, (size_t)ne * sb * sizeof(TB));
+  cudaError_t e = dev_alloc_cuda(s, Bd, (size_t)ne * sb * sizeof(TB));
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(Ao, (size_t)nf * sb * sizeof(TB));
+  e = dev_alloc_cuda(s, Ao, (size_t)nf * sb * sizeof(TB));
   if (e != cudaSuccess) return e;
   k_to_lp<TB><<<1216, 256, 0, st>>>(ne, N * N, sb, Bdiag, static_cast<TB*>(*Bd));
   k_to_lp<TB><<<1216, 256, 0, st>>>(nf, N * N, sb, Aoff, static_cast<TB*>(*Ao));
@@ -340,10 +340,10 @@ static cudaError_t build_lp(int64_t ne, int64_t nf, int N, const double* Bdiag, 
 cudaError_t lp_build_blocks(stdg_solver* s, int kind) {
   cudaError_t e;
   if (kind == STDG_PREC_MIXED_BF16)
-    e = build_lp<__nv_bfloat16>(s->ne, s->nf, s->N, s->Bdiag, s->Aoff, &s->lpB, &s->lpA, &s->lpSB, s->stream);
+    e = build_lp<__nv_bfloat16>(s, s->ne, s->nf, s->N, s->Bdiag, s->Aoff, &s->lpB, &s->lpA, &s->lpSB, s->stream);
   else
-    e = build_lp<float>(s->ne, s->nf, s->N, s->Bdiag, s->Aoff, &s->lpB, &s->lpA, &s->lpSB, s->stream);
-  if (e == cudaSuccess) { s->allocs.push_back(s->lpB); s->allocs.push_back(s->lpA); s->lpkind = kind; }
+    e = build_lp<float>(s, s->ne, s->nf, s->N, s->Bdiag, s->Aoff, &s->lpB, &s->lpA, &s->lpSB, s->stream);
+  if (e == cudaSuccess) s->lpkind = kind;
   return e;
 }
 
@@ -360,12 +360,10 @@ __global__ void k_to_df(int64_t nblk, int NN, int SB, const double* __restrict__
 
 cudaError_t df_build_blocks(stdg_solver* s) {
   const int sb = ((s->N * s->N + 1) / 2) * 2;
-  cudaError_t e = cudaMalloc(&s->dfB, (size_t)s->ne * sb * sizeof(float2));
+  cudaError_t e = dev_alloc_cuda(s, &s->dfB, (size_t)s->ne * sb * sizeof(float2));
   if (e != cudaSuccess) return e;
-  s->allocs.push_back(s->dfB);
-  e = cudaMalloc(&s->dfA, (size_t)s->nf * sb * sizeof(float2));
+  e = dev_alloc_cuda(s, &s->dfA, (size_t)s->nf * sb * sizeof(float2));
   if (e != cudaSuccess) return e;
-  s->allocs.push_back(s->dfA);
   k_to_df<<<1216, 256, 0, s->stream>>>(s->ne, s->N * s->N, sb, s->Bdiag, static_cast<float2*>(s->dfB));
   k_to_df<<<1216, 256, 0, s->stream>>>(s->nf, s->N * s->N, sb, s->Aoff, static_cast<float2*>(s->dfA));
   s->dfSB = sb;

@@ -114,7 +114,7 @@ static stdg_status mesh_build(const double* verts, int64_t nv, const int64_t* te
   M->nf = nf;
   M->left.resize(nf); M->right.resize(nf); M->fl.resize(nf); M->fr.resize(nf);
   M->fverts.resize(3 * nf); M->code_l.resize(nf); M->code_r.resize(nf);
-  M->normal.resize(3 * nf); M->area.resize(nf); M->fcoords.resize(9 * nf);
+  M->normal.resize(3 * nf); M->area.resize(nf); M->fcoords.resize(9 * nf); M->fshift.assign(3 * nf, 0.0);
   M->t2f.assign(4 * ne, -1); M->t2n.assign(4 * ne, -1); M->t2code.assign(4 * ne, -1);
   for (int64_t j = 0; j < nf; ++j) {
     const Rec& r = recs[j];
@@ -143,6 +143,12 @@ static stdg_status mesh_build(const double* verts, int64_t nv, const int64_t* te
     }
     for (int k = 0; k < 3; ++k)
       for (int d = 0; d < 3; ++d) M->fcoords[9 * j + 3 * k + d] = vc(r.l, lv[k], d);
+    if (r.r >= 0 && M->periodic) {
+      // the shared vertex fverts[0] in r's frame against l's frame: a whole number of periods
+      int q0 = -1;
+      for (int q = 0; q < 4; ++q) if (M->T[4 * r.r + q] == M->fverts[3 * j]) q0 = q;
+      for (int d = 0; d < 3; ++d) M->fshift[3 * j + d] = M->fcoords[9 * j + d] - vc(r.r, q0, d);
+    }
     const double* A = &M->fcoords[9 * j];
     const double* B = &M->fcoords[9 * j + 3];
     const double* C = &M->fcoords[9 * j + 6];

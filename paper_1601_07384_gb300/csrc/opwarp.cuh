@@ -361,12 +361,10 @@ static cudaError_t ensure_warp_blocks(stdg_solver* s, void** Bd, void** Ao) {
   using TB = typename W::TB;
   const int N = s->N, NR = warp_nr(N), NP = warp_np(N);
   const size_t per = (size_t)W::kPlanes * NR * NP;
-  cudaError_t e = cudaMalloc(Bd, (size_t)s->ne * per * sizeof(TB));
+  cudaError_t e = dev_alloc_cuda(s, Bd, (size_t)s->ne * per * sizeof(TB));
   if (e != cudaSuccess) return e;
-  s->allocs.push_back(*Bd);
-  e = cudaMalloc(Ao, (size_t)s->nf * per * sizeof(TB));
+  e = dev_alloc_cuda(s, Ao, (size_t)s->nf * per * sizeof(TB));
   if (e != cudaSuccess) return e;
-  s->allocs.push_back(*Ao);
   k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->ne, N, NR, NP, s->Bdiag, static_cast<TB*>(*Bd));
   k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->nf, N, NR, NP, s->Aoff, static_cast<TB*>(*Ao));
   s->nlaunch += 2;
@@ -379,9 +377,8 @@ static cudaError_t ensure_warp_visc_diag(stdg_solver* s, void** Bv) {
   if (*Bv || !s->Bvisc) return cudaSuccess;
   using TB = typename W::TB;
   const int N = s->N, NR = warp_nr(N), NP = warp_np(N);
-  cudaError_t e = cudaMalloc(Bv, (size_t)s->ne * W::kPlanes * NR * NP * sizeof(TB));
+  cudaError_t e = dev_alloc_cuda(s, Bv, (size_t)s->ne * W::kPlanes * NR * NP * sizeof(TB));
   if (e != cudaSuccess) return e;
-  s->allocs.push_back(*Bv);
   k_to_padded<TB, W::kPlanes><<<1216, 256, 0, s->stream>>>(s->ne, N, NR, NP, s->Bdiag, static_cast<TB*>(*Bv), s->Bvisc, -1.0);
   ++s->nlaunch;
   return cudaGetLastError();

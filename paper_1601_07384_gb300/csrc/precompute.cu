@@ -94,19 +94,22 @@ __global__ void __launch_bounds__(256) k_face_blocks(FaceArgs a) {
   double* C1 = G + N * N;
   double* C2 = C1 + N * N;
   const double* fv = a.m.fvx + 9 * (size_t)j;
+  // the dual cell in l(j)'s frame: points of r(j) are shifted by fshift (periodic meshes)
+  const double* sh = a.m.fshift + 3 * (size_t)j;
   if (threadIdx.x == 0) {
     double vt = 0.0, cen[3] = {0, 0, 0};
     for (int s = 0; s < nsides; ++s) {
       int t = s ? r : l;
       double v = a.m.detJ[t] / 24.0;
-      for (int d = 0; d < 3; ++d) cen[d] += v * 0.25 * (fv[d] + fv[3 + d] + fv[6 + d] + a.m.bary[3 * t + d]);
+      for (int d = 0; d < 3; ++d)
+        cen[d] += v * 0.25 * (fv[d] + fv[3 + d] + fv[6 + d] + a.m.bary[3 * t + d] + (s ? sh[d] : 0.0));
       vt += v;
     }
     for (int d = 0; d < 3; ++d) cen[d] /= vt;
     double h = 0.0;
     for (int k = 0; k < 3 + nsides; ++k) {
       const double* P = k < 3 ? fv + 3 * k : a.m.bary + 3 * (k == 3 ? l : r);
-      for (int d = 0; d < 3; ++d) h = fmax(h, fabs(P[d] - cen[d]));
+      for (int d = 0; d < 3; ++d) h = fmax(h, fabs(P[d] + (k == 4 ? sh[d] : 0.0) - cen[d]));
     }
     geo[0] = cen[0]; geo[1] = cen[1]; geo[2] = cen[2]; geo[3] = h;
   }
@@ -120,7 +123,8 @@ __global__ void __launch_bounds__(256) k_face_blocks(FaceArgs a) {
     const double* Jt = a.m.J + 9 * (size_t)t;
     const double* X0 = a.m.X0 + 3 * (size_t)t;
     double x[3];
-    for (int d = 0; d < 3; ++d) x[d] = X0[d] + Jt[3 * d] * xi[0] + Jt[3 * d + 1] * xi[1] + Jt[3 * d + 2] * xi[2];
+    for (int d = 0; d < 3; ++d)
+      x[d] = X0[d] + Jt[3 * d] * xi[0] + Jt[3 * d + 1] * xi[1] + Jt[3 * d + 2] * xi[2] + (s ? sh[d] : 0.0);
     wq[idx] = a.m.detJ[t] * a.r.sub_lin_w[f * nq + q];
     double yx = (x[0] - x0) * hinv, yy = (x[1] - y0) * hinv, yz = (x[2] - z0) * hinv;
     for (int mm = 0; mm < N; ++mm)

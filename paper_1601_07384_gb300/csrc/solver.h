@@ -83,7 +83,21 @@ struct stdg_solver {
   double theta = 1.0;                          // semi-implicit pressure weight (p_t = 0 only)
   double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
   float2 *cphiP = nullptr, *cdphiP = nullptr, *cfphiP = nullptr;   // convection tables as (hi, lo) pairs
-  std::vector<void*> allocs;
+  // device allocations: through the caller's allocator when one was given (stdg_solver_create_alloc),
+  // else cudaMalloc; released in reverse order by stdg_solver_destroy
+  struct Alloc { void* p; size_t bytes; };
+  std::vector<Alloc> allocs;
+  stdg_alloc_fn alloc_fn = nullptr;
+  stdg_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  // initial / boundary data from a host callback (stdg_set_initial_fn, stdg_set_boundary_fn)
+  stdg_vel_fn bc_fn = nullptr;
+  void* bc_user = nullptr;
+  int* bidx = nullptr;                        // compact boundary index of every face, -1 if interior
+  double* bc_table = nullptr;                 // callback values at the boundary points [nbd][npt][3]
+  double* bc_modes = nullptr;                 // device modes of a STDG_FIELD_CURL_MODES boundary field
+  std::vector<double> bc_pts;                 // the boundary points [nbd * npt][4]: x, y, z, tau
+  std::vector<double> bc_xyzt, bc_uvw;        // per-step callback arguments
   stdg::GnnState* gnn = nullptr;
   stdg::MgState* mg = nullptr;               // coarse correction of STDG_SOLVER_KRON_MG (built on first use)
   float *vpcU = nullptr, *vpcLam = nullptr;  // viscous block-Jacobi by fast diagonalisation (viscpc.cu)
@@ -161,6 +175,8 @@ stdg_status gnn_precond(stdg_solver* s, const double* r, double* z, int use_gnn)
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res);
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes);
+cudaError_t dev_alloc_cuda(stdg_solver* s, void** p, size_t bytes);   // the same, as a CUDA error code
+void dev_free(stdg_solver* s, void* p);                                 // early release of one array
 // Agglomeration coarse correction (mg.cu): z += R^T V (R r) on the constant modes of every tet, with
 // partials of r.(R^T V R r) per column written to part[b * Ng + a], b < mg_partial_blocks().
 stdg_status mg_ensure(stdg_solver* s);       // host + device setup, outside stream capture

@@ -182,9 +182,12 @@ __global__ void __launch_bounds__(128) k_boundary(int N, int Ng, int nq, int nqf
                                                   const double* __restrict__ tri_st, const double* __restrict__ tri_w,
                                                   const double* __restrict__ ttau, const double* __restrict__ tw,
                                                   const double* __restrict__ tg, MultiIdx mi, FieldArg fld, double t0,
-                                                  double dt, double* __restrict__ Vbc, double* __restrict__ Gbc) {
+                                                  double dt, const int* __restrict__ bidx, double* __restrict__ Vbc,
+                                                  double* __restrict__ Gbc) {
   const int j = blockIdx.x;
   if (right[j] >= 0) return;
+  // data points of this boundary face (host-callback data): nq*nt sub-tetrahedron points, then nqf*nt face points
+  const int64_t pid0 = (int64_t)bidx[j] * (nq + nqf) * nt;
   extern __shared__ double sm[];
   const int Nst = N * Ng;
   const int CH = 64;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(128) k_boundary(int N, int Ng, int nq, int nqf
         }
         psi_hat(N, mi, Cj, xh, x, tmp + u * N, ps + u * N);
         for (int m = 0; m < N; ++m) ps[u * N + m] *= w;
-        eval_field(fld, x, t0 + ttau[ti] * dt, vv + 3 * u);
+        eval_field(fld, x, t0 + ttau[ti] * dt, pid0 + (pass == 0 ? 0 : (int64_t)nq * nt) + pt, ttau[ti], vv + 3 * u);
         tq[u] = q; tt[u] = ti;
       }
       __syncthreads();
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(128) k_boundary(int N, int Ng, int nq, int nqf
 // ---- initial data: V[j][c][0][m] = Sum_{sides} Sum_q w psi_m v0_c(x_q), other time modes 0
 __global__ void __launch_bounds__(128) k_initial(int N, int Ng, int nq, const int* __restrict__ left,
                                                  const int* __restrict__ right, const double* __restrict__ fvx,
-                                                 const double* __restrict__ bary,
+                                                 const double* __restrict__ fshift, const double* __restrict__ bary,
                                                  const double* __restrict__ C, const double* __restrict__ x0h,
                                                  const double* __restrict__ sub_xi, const double* __restrict__ sub_w,
                                                  MultiIdx mi, FieldArg fld, double* __restrict__ V) {
@@ -268,14 +271,16 @@ __global__ void __launch_bounds__(128) k_initial(int N, int Ng, int nq, const in
       const int i = sd ? right[j] : left[j];
       const double* xi = sub_xi + 3 * (size_t)q;
       const double* fv = fvx + 9 * (size_t)j;
-      const double* bc = bary + 3 * (size_t)i;
+      // the apex of T_ij in l(j)'s frame (r(j)'s barycentre shifted by fshift on periodic meshes)
+      double bc[3];
+      for (int d = 0; d < 3; ++d) bc[d] = bary[3 * (size_t)i + d] + (sd ? fshift[3 * (size_t)j + d] : 0.0);
       double x[3];
       for (int d = 0; d < 3; ++d)
         x[d] = fv[d] + xi[0] * (fv[3 + d] - fv[d]) + xi[1] * (fv[6 + d] - fv[d]) + xi[2] * (bc[d] - fv[d]);
       const double w = subvol6(fv, bc) * sub_w[q];
       psi_hat(N, mi, Cj, xh, x, tmp + u * N, ps + u * N);
       for (int m = 0; m < N; ++m) ps[u * N + m] *= w;
-      eval_field(fld, x, 0.0, vv + 3 * u);
+      eval_field(fld, x, 0.0, (int64_t)j * 2 * nq + pt, 0.0, vv + 3 * u);
     }
     __syncthreads();
     for (int o = threadIdx.x; o < 3 * N; o += blockDim.x) {
@@ -296,6 +301,8 @@ struct ConvArgs {
   const double *phi, *dphi, *w, *fphi, *tri_st, *tri_w, *ttau, *tw, *tg;
   FieldArg fld;
   double t0, dt;
+  const int* bidx;      // compact boundary index per face (points of host-callback data)
+  int bnpt;             // data points per boundary face: (nq + nqf) * nt, face points after nq * nt
   const double* vbar;   // [3][ne][Nst]
   double* ups;          // [3][ne][Nst]
 };
@@ -484,7 +491,8 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2
               vp[c] = s;
             }
           } else {
-            eval_field(a.fld, x, a.t0 + a.ttau[ti] * a.dt, vp);
+            eval_field(a.fld, x, a.t0 + a.ttau[ti] * a.dt,
+                       (int64_t)a.bidx[j] * a.bnpt + (int64_t)a.nq * nt + (int64_t)q * nt + ti, a.ttau[ti], vp);
           }
           const double unm = vm[0] * n0 + vm[1] * n1 + vm[2] * n2;
           const double unp = vp[0] * n0 + vp[1] * n1 + vp[2] * n2;
@@ -542,9 +550,42 @@ __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double
     y[e] = fma(a, x[e], y[e]);
 }
 
-static FieldArg to_arg(const stdg_field& f) {
+static FieldArg to_arg(const stdg_field& f, const double* modes = nullptr) {
   FieldArg a{};
   a.kind = f.kind; a.c[0] = f.c[0]; a.c[1] = f.c[1]; a.c[2] = f.c[2]; a.a = f.a; a.d = f.d; a.nu = f.nu;
+  a.nmodes = f.kind == STDG_FIELD_CURL_MODES ? f.nmodes : 0;
+  a.modes = modes;
+  return a;
+}
+
+// Checks a stdg_field and, for STDG_FIELD_CURL_MODES, uploads its modes as rows (k, A, phi, 2 pi k x A).
+static stdg_status field_prepare(stdg_solver* s, const stdg_field& f, double** modes_dev) {
+  *modes_dev = nullptr;
+  if (f.kind < STDG_FIELD_ZERO || f.kind > STDG_FIELD_CURL_MODES) { set_error("unknown field kind %d", f.kind); return STDG_EINVAL; }
+  if (f.kind != STDG_FIELD_CURL_MODES) return STDG_OK;
+  if (!f.modes || f.nmodes < 1 || f.nmodes > 256) { set_error("STDG_FIELD_CURL_MODES needs 1..256 modes"); return STDG_EINVAL; }
+  std::vector<double> h((size_t)f.nmodes * 10);
+  const double tp = 2.0 * 3.14159265358979323846;
+  for (int m = 0; m < f.nmodes; ++m) {
+    const double* k = f.modes + 7 * m;
+    double* o = h.data() + 10 * m;
+    for (int c = 0; c < 7; ++c) o[c] = k[c];
+    o[7] = tp * (k[1] * k[5] - k[2] * k[4]);
+    o[8] = tp * (k[2] * k[3] - k[0] * k[5]);
+    o[9] = tp * (k[0] * k[4] - k[1] * k[3]);
+  }
+  stdg_status e = dev_alloc(s, (void**)modes_dev, h.size() * sizeof(double));
+  if (e != STDG_OK) return e;
+  if (cudaMemcpy(*modes_dev, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("field mode upload failed"); return STDG_ECUDA;
+  }
+  return STDG_OK;
+}
+
+// boundary data of the current step: the device field kind, or the host callback's table
+static FieldArg bc_arg(const stdg_solver* s) {
+  FieldArg a = to_arg(s->bc, s->bc_modes);
+  if (s->bc_fn) { a.kind = kFieldTable; a.table = s->bc_table; }
   return a;
 }
 
@@ -573,7 +614,7 @@ static stdg_status ensure_step(stdg_solver* s) {
   return ensure_krylov(s);
 }
 
-static cudaError_t boundary_data(stdg_solver* s, double t0) {
+static cudaError_t launch_boundary(stdg_solver* s, double t0, const FieldArg& fld) {
   const int CH = 64;
   size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
   cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -581,9 +622,47 @@ static cudaError_t boundary_data(stdg_solver* s, double t0) {
   k_boundary<<<(int)s->nf, 128, smem, s->stream>>>(
       s->N, s->Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.left, s->dm.right, s->dm.fl, s->dm.bary, s->dm.J,
       s->dm.detJ, s->dm.fvx, s->dm.normal, s->dm.area, s->C, s->x0h, s->dr.tet_nl_xi, s->dr.tet_nl_w,
-      s->dr.tri_nl_st, s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, make_mi(s->p), to_arg(s->bc), t0, s->dt,
+      s->dr.tri_nl_st, s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, make_mi(s->p), fld, t0, s->dt, s->bidx,
       s->Vbc, s->Gbc);
   return cudaGetLastError();
+}
+
+// Boundary data of the slab [t0, t0 + dt]; with a host callback its values at the collected points are
+// evaluated first and uploaded (the previous step ended with a stream synchronisation, so the table
+// and the host buffers are free).
+static stdg_status boundary_data(stdg_solver* s, double t0) {
+  if (s->bc_fn) {
+    const size_t n = s->bc_pts.size() / 4;
+    for (size_t k = 0; k < n; ++k) {
+      for (int c = 0; c < 3; ++c) s->bc_xyzt[4 * k + c] = s->bc_pts[4 * k + c];
+      s->bc_xyzt[4 * k + 3] = t0 + s->bc_pts[4 * k + 3] * s->dt;
+    }
+    s->bc_fn(s->bc_xyzt.data(), (int64_t)n, s->bc_uvw.data(), s->bc_user);
+    if (cudaMemcpyAsync(s->bc_table, s->bc_uvw.data(), n * 3 * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      set_error("boundary data upload failed"); return STDG_ECUDA;
+    }
+  }
+  if (launch_boundary(s, t0, bc_arg(s)) != cudaSuccess) { set_error("boundary data launch failed"); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+static cudaError_t launch_initial(stdg_solver* s, const FieldArg& fld) {
+  const int CH = 64;
+  size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
+  cudaFuncSetAttribute(k_initial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ++s->nlaunch;
+  k_initial<<<(int)s->nf, 128, smem, s->stream>>>(s->N, s->Ng, s->nq_nl, s->dm.left, s->dm.right, s->dm.fvx,
+                                                  s->dm.fshift, s->dm.bary, s->C, s->x0h, s->dr.tet_nl_xi, s->dr.tet_nl_w,
+                                                  make_mi(s->p), fld, s->V);
+  return cudaGetLastError();
+}
+
+static stdg_status initial_done(stdg_solver* s) {
+  cudaMemsetAsync(s->P, 0, (size_t)s->ne * s->Nst * sizeof(double), s->stream);
+  s->t = 0.0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("initial projection failed"); return STDG_ECUDA; }
+  return STDG_OK;
 }
 
 }  // namespace stdg
@@ -595,24 +674,92 @@ extern "C" stdg_status stdg_set_initial(stdg_solver* s, const stdg_field* f) {
   cudaSetDevice(s->device);
   stdg_status e = ensure_step(s);
   if (e != STDG_OK) return e;
-  const int CH = 64;
-  size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
-  cudaFuncSetAttribute(k_initial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  ++s->nlaunch;
-  k_initial<<<(int)s->nf, 128, smem, s->stream>>>(s->N, s->Ng, s->nq_nl, s->dm.left, s->dm.right, s->dm.fvx,
-                                                  s->dm.bary, s->C, s->x0h, s->dr.tet_nl_xi, s->dr.tet_nl_w,
-                                                  make_mi(s->p), to_arg(*f), s->V);
-  STDG_LAUNCH_CHECK();
-  cudaMemsetAsync(s->P, 0, (size_t)s->ne * s->Nst * sizeof(double), s->stream);
-  s->t = 0.0;
-  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("initial projection failed"); return STDG_ECUDA; }
-  return STDG_OK;
+  double* modes = nullptr;
+  if ((e = field_prepare(s, *f, &modes)) != STDG_OK) return e;
+  if (launch_initial(s, to_arg(*f, modes)) != cudaSuccess) { set_error("initial projection launch failed"); return STDG_ECUDA; }
+  e = initial_done(s);
+  if (modes) dev_free(s, modes);
+  return e;
+}
+
+extern "C" stdg_status stdg_set_initial_fn(stdg_solver* s, stdg_vel_fn fn, void* user) {
+  if (!s || !fn) { set_error("stdg_set_initial_fn: NULL argument"); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  stdg_status e = ensure_step(s);
+  if (e != STDG_OK) return e;
+  // the points at which k_initial evaluates the data: one pass recording them, the callback on the
+  // host, then the projection reading the returned values
+  const size_t npts = (size_t)s->nf * 2 * s->nq_nl;
+  double *pts = nullptr, *vals = nullptr;
+  if ((e = dev_alloc(s, (void**)&pts, npts * 4 * sizeof(double))) != STDG_OK) return e;
+  if ((e = dev_alloc(s, (void**)&vals, npts * 3 * sizeof(double))) != STDG_OK) { dev_free(s, pts); return e; }
+  FieldArg fa{};
+  fa.kind = kFieldCollect; fa.collect = pts;
+  cudaMemsetAsync(pts, 0, npts * 4 * sizeof(double), s->stream);
+  std::vector<double> hp(npts * 4), hv(npts * 3, 0.0);
+  cudaError_t ce = launch_initial(s, fa);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp.data(), pts, npts * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce == cudaSuccess) {
+    for (size_t k = 0; k < npts; ++k) hp[4 * k + 3] = 0.0;          // t = 0
+    fn(hp.data(), (int64_t)npts, hv.data(), user);
+    ce = cudaMemcpyAsync(vals, hv.data(), npts * 3 * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  }
+  if (ce == cudaSuccess) {
+    fa.kind = kFieldTable; fa.table = vals; fa.collect = nullptr;
+    ce = launch_initial(s, fa);
+  }
+  e = ce == cudaSuccess ? initial_done(s) : (set_error("initial projection (callback data) failed: %s",
+                                                       cudaGetErrorString(ce)), STDG_ECUDA);
+  cudaStreamSynchronize(s->stream);
+  dev_free(s, vals);
+  dev_free(s, pts);
+  return e;
 }
 
 extern "C" stdg_status stdg_set_boundary(stdg_solver* s, const stdg_field* f) {
   if (!s || !f) { set_error("stdg_set_boundary: NULL argument"); return STDG_EINVAL; }
-  if (f->kind < 0 || f->kind > 2) { set_error("unknown field kind %d", f->kind); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  double* modes = nullptr;
+  stdg_status e = field_prepare(s, *f, &modes);
+  if (e != STDG_OK) return e;
+  if (s->bc_modes) { cudaStreamSynchronize(s->stream); dev_free(s, s->bc_modes); }
   s->bc = *f;
+  s->bc.modes = nullptr;                         // the caller's host array is not kept
+  s->bc_modes = modes;
+  s->bc_fn = nullptr; s->bc_user = nullptr;
+  return STDG_OK;
+}
+
+extern "C" stdg_status stdg_set_boundary_fn(stdg_solver* s, stdg_vel_fn fn, void* user) {
+  if (!s || !fn) { set_error("stdg_set_boundary_fn: NULL argument"); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  stdg_status e = ensure_step(s);
+  if (e != STDG_OK) return e;
+  const size_t npts = (size_t)s->nbd * (s->nq_nl + s->nqf_nl) * s->nt_nl;
+  if (!s->bc_table && npts > 0 && (e = dev_alloc(s, (void**)&s->bc_table, npts * 3 * sizeof(double))) != STDG_OK)
+    return e;
+  double* pts = nullptr;
+  if (npts > 0 && (e = dev_alloc(s, (void**)&pts, npts * 4 * sizeof(double))) != STDG_OK) return e;
+  s->bc_pts.assign(npts * 4, 0.0);
+  if (npts > 0) {
+    // record the boundary points with the kernel that consumes their values (the convection reads the
+    // face points of the same table); Vbc / Gbc are recomputed by the next step
+    FieldArg fa{};
+    fa.kind = kFieldCollect; fa.collect = pts;
+    cudaError_t ce = launch_boundary(s, 0.0, fa);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(s->bc_pts.data(), pts, npts * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    dev_free(s, pts);
+    if (ce != cudaSuccess) { set_error("boundary point collection failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  }
+  s->bc_xyzt.assign(npts * 4, 0.0);
+  s->bc_uvw.assign(npts * 3, 0.0);
+  if (s->bc_modes) { dev_free(s, s->bc_modes); s->bc_modes = nullptr; }
+  s->bc = stdg_field{};
+  s->bc.kind = STDG_FIELD_ZERO;
+  s->bc_fn = fn; s->bc_user = user;
   return STDG_OK;
 }
 
@@ -668,7 +815,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   // previous slab average and new-slab boundary data
   ++s->nlaunch;
   k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar_n);
-  if (boundary_data(s, s->t) != cudaSuccess) { set_error("boundary data launch failed"); return STDG_ECUDA; }
+  if ((e = boundary_data(s, s->t)) != STDG_OK) return e;
   // step 0: v^{n+1,0}(x, tau) = v^n(x, 1), p^{n+1,0} = 0
   ++s->nlaunch;
   k_trace<<<1216, 256, 0, st>>>(nf, N, Ng, s->dm.right, g1, s->V, s->Vbc, s->vtmp);
@@ -713,7 +860,8 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
                 s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
                 s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
-                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, to_arg(s->bc), s->t, s->dt, s->Vbar, s->Ups};
+                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, bc_arg(s), s->t, s->dt, s->bidx,
+                (s->nq_nl + s->nqf_nl) * s->nt_nl, s->Vbar, s->Ups};
     ++s->nlaunch;
     k_convection<<<ne, kConvCH, conv_smem, st>>>(ca, s->cphiP, s->cdphiP, s->cfphiP);
     phase_mark(s, 2);

@@ -2,7 +2,10 @@
 
 Tolerances: one operator application in FP64 agrees to 1e-12 relative (max-norm over the
 output, scaled by the output's max); solves are compared through residuals measured with the
-oracle's operator and against the oracle's direct solution within cond * tol."""
+oracle's operator and against the oracle's direct solution within cond * tol; a full time step
+(pressure and velocity coefficients) agrees to 1e-10 relative when both sides solve to 1e-13
+(the GPU iteratively, the oracle by sparse LU)."""
+import functools
 import numpy as np
 import pytest
 
@@ -15,6 +18,7 @@ from oracle.blocks import SpaceTimeDG
 from oracle.mesh import Mesh
 from oracle.step import initial_state, time_step
 
+STEP_TOL = 1e-10          # relative, pressure and velocity coefficients after each FP64 step
 CASES = [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2), (3, 2, 0)]
 
 
@@ -101,9 +105,11 @@ def test_update_rhs_and_moments_match_oracle(n, p, pt):
     assert rel(b, -Ad) <= 1e-11
 
 
-@pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1)])
-@pytest.mark.parametrize("method", ["kron_cg", "gmres"])
+@pytest.mark.parametrize("n,p,pt,method", [(n, p, pt, m) for (n, p, pt) in [(3, 1, 0), (2, 2, 1), (2, 3, 1)]
+                                            for m in ["kron_cg", "gmres"]] + [(3, 1, 0, "cg"), (3, 2, 0, "cg")])
 def test_solve_matches_direct(n, p, pt, method):
+    """The paper's solvers (GMRES; CG on -A for p_t = 0, Cor. 1-2) and the Kronecker-decoupled CG
+    against the oracle's sparse-direct solution of the same pinned system."""
     from scipy.sparse.linalg import spsolve
     gs, d = setup(n, p, pt, restart=50, max_iters=50000)
     b = np.random.default_rng(3).standard_normal((d.mesh.ne, d.Nst))
@@ -143,7 +149,7 @@ def test_step_matches_oracle(p, pt, npic, precision):
     # initial projection agrees (through basis-independent moments)
     so1 = time_step(d, so, prm.nu, npic, lambda x, tt: beltrami_velocity(x, tt, prm), tol=1e-13, method="direct")
     assert abs(t - 0.01) < 1e-15
-    assert rel(P.cpu().numpy(), so1.P.ravel()) <= 1e-9
+    assert rel(P.cpu().numpy(), so1.P.ravel()) <= STEP_TOL
     U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
     Uo = np.zeros_like(U)
     for j in range(d.mesh.nf):
@@ -170,7 +176,7 @@ def test_theta_steps_match_oracle(theta):
         gs.step(prm.nu, 2, method="kron_cg", tol=1e-13)
         so = time_step(d, so, prm.nu, 2, vbc, tol=1e-13, method="direct", theta=theta)
     P, V, t = gs.get_state()
-    assert rel(P.cpu().numpy(), so.P.ravel()) <= 1e-9
+    assert rel(P.cpu().numpy(), so.P.ravel()) <= STEP_TOL
     U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
     Uo = np.zeros_like(U)
     for j in range(d.mesh.nf):
@@ -331,7 +337,7 @@ def test_step_with_coarse_correction_matches_oracle(precision):
     P, V, _ = gs.get_state()
     so = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
     so1 = time_step(d, so, prm.nu, 2, lambda x, tt: beltrami_velocity(x, tt, prm), tol=1e-13, method="direct")
-    assert rel(P.cpu().numpy(), so1.P.ravel()) <= 1e-9
+    assert rel(P.cpu().numpy(), so1.P.ravel()) <= STEP_TOL
     U = gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
     Uo = np.zeros_like(U)
     for j in range(d.mesh.nf):
@@ -389,7 +395,7 @@ def test_step_with_previous_viscous_solvers():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, STDG_VISC_SOLVER="gmres")
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(root, "tests", "test_gpu_parity.py"), "-q",
-                        "-m", "gpu", "-k", "test_step_matches_oracle and fp64"],
+                        "-m", "gpu", "-k", "test_step_matches_oracle and not benchmarked and fp64"],
                        capture_output=True, text=True, timeout=900, cwd=root, env=env)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     assert "2 passed" in r.stdout
@@ -410,3 +416,81 @@ def test_tma_operator_kernels_match_oracle(prec, tol, monkeypatch):
         y = gs.pressure_apply(torch.from_numpy(x).cuda()).cpu().numpy()
         yo = ops.pressure_apply(d, x).ravel()
     assert rel(y, yo) <= tol
+
+
+# ------------------------------------------------------------------ steps at the benchmarked degrees
+def _moments(gs, d, V):
+    return gs.velocity_moments(V).cpu().numpy().reshape(d.mesh.nf, 2, 3, d.Nst)
+
+
+def _oracle_moments(d, V):
+    U = np.zeros((d.mesh.nf, 2, 3, d.Nst))
+    for j in range(d.mesh.nf):
+        fb = d.face_blocks(j)
+        for s_ in range(len(fb["sides"])):
+            U[j, s_] = (fb["Mij"][s_] @ V[j].T).T
+    return U
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_beltrami_step(p, pt, npic, nu, dt):
+    """The oracle's step from the projected Beltrami field on the 48-tet mesh (sparse LU solves)."""
+    v, t = kuhn_mesh(2, seed=0)
+    d = SpaceTimeDG(Mesh(v, t), p, pt, dt)
+    prm = BeltramiParams(nu=nu)
+    so = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    so1 = time_step(d, so, nu, npic, lambda x, tt: beltrami_velocity(x, tt, prm), tol=1e-13, method="direct")
+    return d, so1, _oracle_moments(d, so1.V)
+
+
+@pytest.mark.parametrize("p,pt,npic", [(3, 1, 3), (4, 4, 2)])
+@pytest.mark.parametrize("precision,method", [("fp64", "kron_cg"), ("df32", "kron_mg"), ("mixed_f32", "kron_mg"),
+                                              ("df32", "kron_pcg")])
+def test_step_matches_oracle_at_benchmarked_degrees(p, pt, npic, precision, method):
+    """A full Picard step (Sec. 2.6) at the degrees the benchmark runs: p = 3, p_t = 1 (N = 20: the
+    <20,2> viscous fast-diagonalisation, the N = 20 binary32 operator and convection) and
+    p = p_t = 4 (N = 35, Ng = 5).  Both sides solve to 1e-13; pressure and velocity to 1e-10."""
+    import paper_1601_07384_gb300 as g
+    nu, dt = 0.1, 0.01
+    d, so1, Uo = _oracle_beltrami_step(p, pt, npic, nu, dt)
+    prm = BeltramiParams(nu=nu)
+    v, t = kuhn_mesh(2, seed=0)
+    gs = g.Solver(g.Mesh(v, t), g.Reference(p, pt), dt, precision=precision)
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    st = gs.step(nu, npic, method=method, tol=1e-13)
+    P, V, _ = gs.get_state()
+    ep = rel(P.cpu().numpy(), so1.P.ravel())
+    ev = rel(_moments(gs, d, V), Uo)
+    print(f"p={p} pt={pt} {precision}/{method}: pressure {ep:.2e} velocity {ev:.2e} iters {st['press_iters']}")
+    assert ep <= STEP_TOL and ev <= STEP_TOL
+    # the solvers stop on their recurrence residual; the true residual of the returned x (reported)
+    # stays within a small multiple of it at this tolerance, 3e-12 measured
+    assert max(st["press_residual"]) <= 1e-11
+
+
+@pytest.mark.parametrize("tol,bound", [(1e-13, STEP_TOL), (1e-12, 1e-8)])
+def test_tiny_configuration_five_steps(tol, bound):
+    """The tiny configuration end to end: 3^3 hexahedra x 6 = 162 jittered tets, p = 1, p_t = 0,
+    nu = 0.1, dt = 0.01, 5 steps of 2 Picard iterations, FP64, the paper's CG on the system with the
+    pressure pinned at one point, Beltrami data; compared with the oracle (sparse LU) after every step.
+    At the configuration's CG tolerance 1e-12 the deviation is bounded by cond * 1e-12; with both
+    sides at 1e-13 it meets the 1e-10 step tolerance."""
+    import paper_1601_07384_gb300 as g
+    prm = BeltramiParams(nu=0.1)
+    gs, d = setup(3, 1, 0, dt=0.01)
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    so = initial_state(d, lambda x: beltrami_velocity(x, 0.0, prm))
+    vbc = lambda x, tt: beltrami_velocity(x, tt, prm)
+    worst = []
+    for k in range(5):
+        st = gs.step(prm.nu, 2, method="cg", tol=tol)
+        so = time_step(d, so, prm.nu, 2, vbc, tol=1e-13, method="direct")
+        P, V, t = gs.get_state()
+        ep, ev = rel(P.cpu().numpy(), so.P.ravel()), rel(_moments(gs, d, V), _oracle_moments(d, so.V))
+        worst.append((ep, ev))
+        assert abs(t - so.t) < 1e-14
+        assert ep <= bound and ev <= bound, (k, ep, ev)
+        assert max(st["press_residual"]) <= tol
+    print("per-step (pressure, velocity) deviation:", [f"{a:.1e}/{b:.1e}" for a, b in worst])

@@ -1,7 +1,8 @@
 """stdg_solve_noalloc -- the pressure solve for callers that may not allocate device memory
 while running (their device memory belongs to another allocator, or allocation latency is not
 acceptable in their loop).  It must give what stdg_solve(KRON_CG) gives, call after call, with
-its work vectors in the library's fixed device array.  This file is collected last on purpose."""
+its work vectors in the library's fixed device array, and solve the oracle's pinned system.
+This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -38,6 +39,42 @@ def test_noalloc_solve_matches_solve_twice_in_a_row(n, p, pt):
         xr, xn = x_ref.cpu().numpy(), x.cpu().numpy()
         assert np.abs(xn - xr).max() <= 1e-12 * np.abs(xr).max(), call
         assert st["rel_residual"] <= 2e-12 and st["iterations"] == st_ref["iterations"]
+
+
+@pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (3, 2, 1)])
+def test_noalloc_on_a_fresh_solver_matches_oracle_and_allocates_nothing(n, p, pt):
+    """First call on a solver that never ran stdg_solve (no Krylov vectors exist): the solution of
+    the oracle's pinned system (sparse LU) within cond * tol; after the one call that resolves the
+    array's address, a call changes neither free device memory nor the caller's allocator."""
+    from scipy.sparse.linalg import spsolve
+    from inputs import kuhn_mesh
+    from oracle import operators as ops
+    from oracle.blocks import SpaceTimeDG
+    from oracle.mesh import Mesh
+    s = make(n, p, pt)
+    v, t = kuhn_mesh(n, seed=0)
+    d = SpaceTimeDG(Mesh(v, t), p, pt, 0.01)
+    A = ops.pressure_sparse(d)
+    rng = np.random.default_rng(40 + n + p)
+    tol = 1e-12
+    cond = np.linalg.cond(A.toarray())
+    for call in range(3):
+        b = rng.standard_normal((d.mesh.ne, d.Nst))
+        b[0, ops.pin_index(d)] = 0.0
+        bt = torch.from_numpy(b.ravel()).cuda()
+        x = torch.zeros_like(bt)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        n0 = s.alloc_stats()[1]
+        x, st = s.solve_noalloc(bt, x, tol=tol)
+        torch.cuda.synchronize()
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert s.alloc_stats()[1] == n0
+        xn = x.cpu().numpy()
+        assert np.linalg.norm(b.ravel() - A @ xn) <= 2 * tol * np.linalg.norm(b)
+        xd = spsolve(A.tocsc(), b.ravel())
+        assert np.linalg.norm(xn - xd) <= 10 * cond * tol * np.linalg.norm(xd)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
