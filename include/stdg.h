@@ -406,6 +406,15 @@ stdg_status stdg_gnn_autoharvest(stdg_solver* s, int nsnap, int every, int max_p
 stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int batch, double* first_loss,
                            double* last_loss);
 
+/* The product behind the network's dense layers when its weights are bfloat16 (the learned
+ * preconditioner above; the paper has no counterpart): D[m * ldd + n] = Sum_k A[m * lda + k] B[n * ldb + k]
+ * for m < M, n < N, k < K, with A and B (binary32, device) rounded to bfloat16 and the products summed
+ * in binary32 on the tensor cores (tcgen05.mma, kind::f16, accumulator in tensor memory).
+ * 1 <= N <= 256 (STDG_EINVAL otherwise); work on `stream`, synchronised before return; STDG_ETIMEOUT
+ * if a bounded wait for the tensor cores gave up.  Allocates one word of device memory per call. */
+stdg_status stdg_tc_gemm_bf16(const float* A_dev, int64_t lda, const float* B_dev, int64_t ldb, float* D_dev,
+                              int64_t ldd, int M, int N, int K, void* stream);
+
 /* ---------------------------------------------------------------- profiling */
 typedef struct {
   int64_t kernel_launches;   /* CUDA kernels this library launched since stdg_profile      */

@@ -152,6 +152,20 @@ class Reference:
             self._h = None
 
 
+def tc_gemm_bf16(A, B):
+    """D = A B^T on the tensor cores (stdg_tc_gemm_bf16): A (M, K), B (N, K) contiguous float32 CUDA
+    tensors, rounded to bfloat16; binary32 sums; N <= 256."""
+    torch = _torch()
+    assert A.is_cuda and B.is_cuda and A.dtype == torch.float32 and B.dtype == torch.float32
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    _lib.check(_lib.load().stdg_tc_gemm_bf16(_ptr(A), K, _ptr(B), K, _ptr(D), N, M, N, K,
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return D
+
+
 def tet_rule(n):
     """Collapsed Gauss-Jacobi tetrahedron rule of the library (host code)."""
     xi = np.empty((n ** 3, 3)); w = np.empty(n ** 3)

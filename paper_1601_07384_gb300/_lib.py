@@ -102,6 +102,7 @@ SIGNATURES = {
     "stdg_gnn_train": (C.c_int, [P, C.c_int, C.c_double, C.c_int, DP, DP]),
     "stdg_gnn_autoharvest": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
     "stdg_profile_read": (C.c_int, [P, C.POINTER(ProfileStats)]),
+    "stdg_tc_gemm_bf16": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P]),
     "stdg_last_error": (C.c_char_p, []),
     "stdg_version": (C.c_char_p, []),
 }

@@ -83,6 +83,8 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
     if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = s->mix_inner_mg = std::atoi(mi);
     const char* mm = std::getenv("STDG_MIXED_M");       // directions kept by the outer flexible CG
     if (mm && std::atoi(mm) > 0 && std::atoi(mm) <= 16) s->mix_m = std::atoi(mm);
+    const char* dw = std::getenv("STDG_DF_MIN_WARPS");  // pair kernel used when this many warps fit per SM
+    if (dw && std::atoi(dw) > 0 && std::atoi(dw) <= 64) s->df_min_warps = std::atoi(dw);
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;
@@ -180,7 +182,7 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
   if (ce == cudaSuccess) ce = launch_assemble(d, s->N, s->Q, s->Aoff, s->Bdiag, s->Bvisc, s->stream);
   // pair blocks (DF32, and the mixed modes' outer and viscous operators), unless the pair kernel would
   // run fewer than 6 warps per SM at this N, Ng: there the binary64 kernel is faster and serves instead
-  if (ce == cudaSuccess && s->opt.precision != STDG_PREC_FP64 && (!s->op_warp || warp_df_warps_per_sm(s) >= 6))
+  if (ce == cudaSuccess && s->opt.precision != STDG_PREC_FP64 && (!s->op_warp || warp_df_warps_per_sm(s) >= s->df_min_warps))
     ce = s->op_warp ? warp_prepare(s, STDG_PREC_DF32) : df_build_blocks(s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) {

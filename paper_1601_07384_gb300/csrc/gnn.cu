@@ -297,9 +297,21 @@ template <typename TW>
 static void dense(stdg_solver* s, int K, int O, const float* A, const void* W, int wt, const float* b, int acc, int relu,
                   float* pre, float* Y) {
   const int ne = (int)s->ne;
+  ++s->nlaunch;
+  if constexpr (sizeof(TW) == 2) {
+    // bfloat16 weights: the product on the tensor cores (activations rounded to bfloat16, binary32 sums)
+    TcGemmArgs a{};
+    a.M = ne; a.N = O; a.K = K; a.ksplit = 0;
+    a.A = A; a.sAm = K; a.sAk = 1;
+    a.B = W; a.b_bf16 = 1;
+    if (wt) { a.sBn = 1; a.sBk = O; } else { a.sBn = K; a.sBk = 1; }
+    a.D = Y; a.ldd = O; a.dsplit = 0;
+    a.bias = b; a.accumulate = acc; a.relu = relu; a.pre = pre; a.err = s->derr;
+    launch_tc_gemm(a, S(s));
+    return;
+  }
   dim3 grid((ne + kT - 1) / kT, (O + kT - 1) / kT);
   k_dense<TW><<<grid, 256, 0, S(s)>>>(ne, K, O, A, static_cast<const TW*>(W), wt, b, acc, relu, pre, Y);
-  ++s->nlaunch;
 }
 static void dense_any(stdg_solver* s, int K, int O, const float* A, int64_t woff, int wt, const float* b, int acc,
                       int relu, float* pre, float* Y) {
@@ -311,8 +323,19 @@ static void wgrad(stdg_solver* s, int O, int K, const float* D, const float* Xin
   GnnState& n = *s->gnn;
   const int ne = (int)s->ne;
   const int nchunk = (ne + kChunk - 1) / kChunk;
-  dim3 grid(nchunk, (O + kT - 1) / kT, (K + kT - 1) / kT);
-  k_wgrad<<<grid, 256, 0, S(s)>>>(ne, O, K, D, Xin, n.wpart);
+  if (n.bf16 && K + 1 <= 256) {
+    // on the tensor cores: part[chunk][o][k] = Sum_{i in chunk} D[i][o] X[i][k], k = K the bias column
+    TcGemmArgs a{};
+    a.M = O; a.N = K + 1; a.K = ne; a.ksplit = kChunk;
+    a.A = D; a.sAm = 1; a.sAk = O;
+    a.B = Xin; a.sBn = 1; a.sBk = K; a.b_bf16 = 0; a.b_ones_last = 1;
+    a.D = n.wpart; a.ldd = K + 1; a.dsplit = (int64_t)O * (K + 1);
+    a.err = s->derr;
+    launch_tc_gemm(a, S(s));
+  } else {
+    dim3 grid(nchunk, (O + kT - 1) / kT, (K + kT - 1) / kT);
+    k_wgrad<<<grid, 256, 0, S(s)>>>(ne, O, K, D, Xin, n.wpart);
+  }
   k_wgrad_reduce<<<kGB, 256, 0, S(s)>>>(nchunk, O, K, n.wpart, 1.0f, n.g + goff, gboff >= 0 ? n.g + gboff : nullptr);
   s->nlaunch += 2;
 }

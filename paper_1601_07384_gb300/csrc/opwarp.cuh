@@ -95,6 +95,14 @@ __device__ __forceinline__ void warp_chunk(const TB* B, int stride, uint32_t pla
   }
 }
 
+// One warp per tet, persistent over a strided stream of tets.  Lane 0 stages the tet's five blocks
+// (its diagonal block and the face blocks of its interior faces) by 1-D TMA bulk copies; all lanes
+// stage the x rows of the tet and its neighbours by cp.async.  binary32 x goes straight into rows of
+// NR entries ([slot][time column][NR], the padding entries zeroed once and never written), the layout
+// the products read; binary64 x (pair policy) is split into (hi, lo) planes of the same layout.
+// Rows 0..31 of the output: lane k owns row k over all five blocks and all time columns.  Rows
+// 32..N-1 (N = 35 at p = 4): one group of 8 lanes per row, each lane summing its share of the four-
+// entry chunks, the group reduced by shuffles at the end.  No block-wide barrier anywhere.
 template <typename W, int NG, int NC>
 __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typename W::XIn* __restrict__ x,
                                                     typename W::YOut* __restrict__ y) {
@@ -102,11 +110,10 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   using XIn = typename W::XIn;
   using Real = typename W::Real;
   constexpr bool kDF = W::kPlanes == 2;
-  constexpr bool kDirectZ = !kDF && NC != 0 && NC % 4 == 0;
   extern __shared__ __align__(128) unsigned char wsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   unsigned char* base = wsm + (size_t)warp * a.warp_bytes;
-  float* zs = reinterpret_cast<float*>(base + a.z_off);
+  float* zs = reinterpret_cast<float*>(base + a.z_off);        // pair policy: (hi, lo) planes of z
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + a.bar_off);
   // NC != 0: N known at compile time (row loops fully unrolled, shared-memory offsets immediate)
   const int N = NC ? NC : a.N, NR = NC ? warp_nr_c(NC) : a.NR, NP = NC ? warp_np_c(NC) : a.NP;
@@ -119,8 +126,14 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
 #pragma unroll
   for (int c = 0; c < NG * NG; ++c) tacc[c] = (Real)a.Tacc[c];
   const int zplane = 5 * NG * NR;
-  const int ZR = kDirectZ ? N : NR;                 // row stride of z
-  for (int e = lane; e < W::kPlanes * zplane; e += 32) zs[e] = 0.0f;     // padding entries stay 0
+  if constexpr (kDF) {
+    for (int e = lane; e < 2 * zplane; e += 32) zs[e] = 0.0f;            // padding entries stay 0
+  } else {
+    for (int st = 0; st < S; ++st) {
+      float* xz = reinterpret_cast<float*>(base + (size_t)st * a.stage_bytes + a.xraw_off);
+      for (int e = lane; e < zplane; e += 32) xz[e] = 0.0f;
+    }
+  }
   if (lane == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bar[s], 33);   // lane 0's expect_tx + 32 cp.async arrivals
     fence_async_smem();
@@ -152,7 +165,14 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
       const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
       if (nb < 0) continue;
       const XIn* src = x + (size_t)nb * Nst;
-      for (int o = lane; o < Nst; o += 32) cp_async<sizeof(XIn)>(xr + sl * Nst + o, src + o);
+      if constexpr (kDF) {
+        for (int o = lane; o < Nst; o += 32) cp_async<sizeof(XIn)>(xr + sl * Nst + o, src + o);
+      } else {
+        for (int o = lane; o < Nst; o += 32) {
+          const int q = o / N, l = o - q * N;
+          cp_async<sizeof(XIn)>(xr + (sl * NG + q) * NR + l, src + o);
+        }
+      }
     }
     cp_async_mbar_arrive_noinc(&bar[st]);
   };
@@ -191,21 +211,12 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
     }
     if (__any_sync(0xffffffffu, abort)) { abort = true; break; }
     __syncwarp();
-    const unsigned char* sb = base + (size_t)st * a.stage_bytes;
-    const XIn* xr = reinterpret_cast<const XIn*>(sb + a.xraw_off);
+    unsigned char* sb = base + (size_t)st * a.stage_bytes;
+    XIn* xr = reinterpret_cast<XIn*>(sb + a.xraw_off);
     const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
     const int nn[4] = {gn.x, gn.y, gn.z, gn.w};
-    // x rows -> z planes (binary32, or the (hi, lo) split); pinned entries read as 0.  With
-    // binary32 x and rows already a multiple of 4 long, z is read in place from the staged rows.
-    if constexpr (kDirectZ) {
-      if (a.pinned) {
-#pragma unroll
-        for (int sl = 0; sl < 5; ++sl) {
-          const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
-          if (nb == 0 && lane < NG) const_cast<XIn*>(xr)[sl * Nst + lane * N] = (XIn)0;
-        }
-      }
-    } else {
+    // pinned entries (constant mode of tet 0, every time column) read as 0
+    if constexpr (kDF) {
 #pragma unroll
       for (int sl = 0; sl < 5; ++sl) {
         const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
@@ -215,18 +226,21 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
           for (int l = lane; l < N; l += 32) {
             XIn v = xr[sl * Nst + q * N + l];
             if (pinned && nb == 0 && l == 0) v = (XIn)0;
+            const float2 hl = df_split(v);
             float* zq = zs + (sl * NG + q) * NR + l;
-            if constexpr (kDF) {
-              const float2 hl = df_split(v);
-              zq[0] = hl.x;
-              zq[zplane] = hl.y;
-            } else {
-              zq[0] = v;
-            }
+            zq[0] = hl.x;
+            zq[zplane] = hl.y;
           }
+      }
+    } else if (pinned) {
+#pragma unroll
+      for (int sl = 0; sl < 5; ++sl) {
+        const int nb = sl == 0 ? i : (fj[sl - 1] >= 0 ? nn[sl - 1] : -1);
+        if (nb == 0 && lane < NG) xr[(sl * NG + lane) * NR] = (XIn)0;
       }
     }
     __syncwarp();
+    const float* zb = kDF ? zs : reinterpret_cast<const float*>(xr);   // z rows [slot][q][NR]
     const TB* blk = reinterpret_cast<const TB*>(sb);
     const int blk_elems = (int)(a.blk_bytes / sizeof(TB));
     int pres = 1, trm = 0;                        // per slot: block present / read transposed
@@ -235,27 +249,53 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
       pres |= (fj[f] >= 0 ? 1 : 0) << (f + 1);
       trm |= (fj[f] >= 0 && (fj[f] & 1) ? 1 : 0) << (f + 1);
     }
-    for (int k = lane; k < N; k += 32) {
+    // output row k of tet i from its sums v over the five blocks: time mixing, scale, mass term,
+    // pin, store, x.y partials
+    auto finish = [&](int k, const Real (&v)[NG]) {
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        Real o = v[q];
+        if (!kron) {
+          o = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) o += tacc[q * NG + b] * v[b];
+        }
+        o *= scale;
+        if (has_mass) {                           // x_i as staged (binary64 for the pair policy)
+          Real m = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b)
+            m += (Real)a.Kmass[q * NG + b] * (Real)(kDF ? xr[b * N + k] : xr[b * NR + k]);
+          o += (Real)(a.mass_coef * a.detJ[i]) * m;
+        }
+        if (pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
+        y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
+        if (a.dotpart) dacc[q] += (float)((Real)x[(size_t)i * Nst + q * N + k] * o);
+      }
+    };
+    const int nmain = N < 32 ? N : 32;
+    if (lane < nmain) {
+      const int k = lane;
       float h0[NG], l0[NG], h1[NG], l1[NG];       // two accumulator chains per time column
 #pragma unroll
       for (int q = 0; q < NG; ++q) { h0[q] = h1[q] = 0.0f; l0[q] = l1[q] = 0.0f; }
       for (int sl = 0; sl < 5; ++sl) {
         if (!((pres >> sl) & 1)) continue;
         const TB* B = blk + sl * blk_elems;
-        const float* z = kDirectZ ? reinterpret_cast<const float*>(xr) + sl * Nst : zs + sl * NG * NR;
+        const float* z = zb + sl * NG * NR;
         if (!((trm >> sl) & 1)) {                 // row k of the block, 4 entries per vector load
           const TB* Br = B + k * NP;
 #pragma unroll
           for (int l = 0; l < NR; l += 8) {
-            warp_chunk<kDF, NG>(Br + l, 1, a.plane_elems, z + l, ZR, zplane, h0, l0);
-            if (l + 4 < NR) warp_chunk<kDF, NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, ZR, zplane, h1, l1);
+            warp_chunk<kDF, NG>(Br + l, 1, a.plane_elems, z + l, NR, zplane, h0, l0);
+            if (l + 4 < NR) warp_chunk<kDF, NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
           }
         } else {                                  // column k: A_rl = A_lr^T, one word per lane
           const TB* Bc = B + k;
 #pragma unroll
           for (int l = 0; l < NR; l += 8) {
-            warp_chunk<kDF, NG>(Bc + l * NP, NP, a.plane_elems, z + l, ZR, zplane, h0, l0);
-            if (l + 4 < NR) warp_chunk<kDF, NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, ZR, zplane, h1, l1);
+            warp_chunk<kDF, NG>(Bc + l * NP, NP, a.plane_elems, z + l, NR, zplane, h0, l0);
+            if (l + 4 < NR) warp_chunk<kDF, NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
           }
         }
       }
@@ -270,25 +310,48 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
           v[q] = (h0[q] + l0[q]) + (h1[q] + l1[q]);
         }
       }
+      finish(k, v);
+    }
+    if (N > 32) {                                 // rows 32 .. N-1: 8 lanes per row, chunks split
+      const int g = lane >> 3, c = lane & 7, r = 32 + g;
+      const int nch = NR / 4;
+      float eh[NG], el[NG];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) { eh[q] = 0.0f; el[q] = 0.0f; }
+      if (r < N) {
+        for (int sl = 0; sl < 5; ++sl) {
+          if (!((pres >> sl) & 1)) continue;
+          const TB* B = blk + sl * blk_elems;
+          const float* z = zb + sl * NG * NR;
+          const bool tr = (trm >> sl) & 1;
+          for (int ch = c; ch < nch; ch += 8) {
+            const int l = 4 * ch;
+            if (!tr) warp_chunk<kDF, NG>(B + r * NP + l, 1, a.plane_elems, z + l, NR, zplane, eh, el);
+            else warp_chunk<kDF, NG>(B + l * NP + r, NP, a.plane_elems, z + l, NR, zplane, eh, el);
+          }
+        }
+      }
+      Real v[NG];
 #pragma unroll
       for (int q = 0; q < NG; ++q) {
-        Real o = v[q];
-        if (!kron) {
-          o = 0;
+        float h = eh[q], e = el[q];
+        if constexpr (!kDF) { h += e; e = 0.0f; }
 #pragma unroll
-          for (int b = 0; b < NG; ++b) o += tacc[q * NG + b] * v[b];
+        for (int o = 4; o > 0; o >>= 1) {         // within the 8-lane group
+          const float oh = __shfl_xor_sync(0xffffffffu, h, o), oe = __shfl_xor_sync(0xffffffffu, e, o);
+          if constexpr (kDF) {
+            float s, t;
+            df_two_sum(h, oh, s, t);
+            h = s;
+            e = e + oe + t;
+          } else {
+            h += oh;
+          }
         }
-        o *= scale;
-        if (has_mass) {                           // x_i as staged (binary64 for the pair policy)
-          Real m = 0;
-#pragma unroll
-          for (int b = 0; b < NG; ++b) m += (Real)a.Kmass[q * NG + b] * (Real)xr[b * N + k];
-          o += (Real)(a.mass_coef * a.detJ[i]) * m;
-        }
-        if (pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
-        y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
-        if (a.dotpart) dacc[q] += (float)((Real)x[(size_t)i * Nst + q * N + k] * o);
+        if constexpr (kDF) v[q] = (double)h + (double)e;
+        else v[q] = h;
       }
+      if (c == 0 && r < N) finish(r, v);
     }
     __syncwarp();
     if (S == 1 && inx < a.ne) {                   // one stage: the next tet's copies start now
@@ -384,15 +447,18 @@ static cudaError_t ensure_warp_visc_diag(stdg_solver* s, void** Bv) {
   return cudaGetLastError();
 }
 
+// Per warp: S stages of [5 blocks | x], then (pair policy only) the (hi, lo) z planes, then the S
+// mbarriers.  binary32 x is staged in rows of NR entries per time column, binary64 x as it is.
 static WarpArgs warp_layout(const stdg_solver* s, size_t tb, int planes, size_t xin, int S) {
   WarpArgs a{};
   a.ne = (int)s->ne; a.N = s->N; a.NR = warp_nr(s->N); a.NP = warp_np(s->N); a.Nst = s->Nst; a.S = S;
   a.plane_elems = (uint32_t)(a.NR * a.NP);
   a.blk_bytes = (uint32_t)(planes * a.plane_elems * tb);
   a.xraw_off = 5 * a.blk_bytes;
-  a.stage_bytes = a.xraw_off + a16((size_t)5 * s->Nst * xin);
+  const bool df = planes == 2;
+  a.stage_bytes = a.xraw_off + (df ? a16((size_t)5 * s->Nst * xin) : a16((size_t)5 * s->Ng * a.NR * xin));
   a.z_off = S * a.stage_bytes;
-  a.bar_off = a.z_off + a16((size_t)planes * 5 * s->Ng * a.NR * sizeof(float));
+  a.bar_off = a.z_off + (df ? a16((size_t)planes * 5 * s->Ng * a.NR * sizeof(float)) : 0);
   a.warp_bytes = a16(a.bar_off + 2 * sizeof(uint64_t));
   return a;
 }

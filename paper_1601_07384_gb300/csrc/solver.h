@@ -58,6 +58,7 @@ struct stdg_solver {
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
+  int df_min_warps = 6;                       // the pair kernel serves where this many warps fit per SM
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
@@ -186,6 +187,20 @@ int mg_launches(const stdg_solver* s);       // kernel launches per application
 int mg_partial_blocks();
 int mg_levels(const stdg_solver* s, int* sizes, int cap);
 void mg_free(stdg_solver* s);
+// Dense layer products on the tensor cores (tcgemm.cu): D (+)= A B^T with bfloat16 operands
+struct TcGemmArgs {
+  int M, N, K, ksplit;                       // CTA (x, z) covers rows [128 x, ...) and k in [z ksplit, ...)
+  const float* A; int64_t sAm, sAk;          // A(m, k) = A[m sAm + k sAk]
+  const void* B; int64_t sBn, sBk;           // B(n, k) = B[n sBn + k sBk]
+  int b_bf16;                                // B elements are bfloat16 (else binary32)
+  int b_ones_last;                           // B(N - 1, k) = 1 (a bias column of a weight gradient)
+  float* D; int64_t ldd, dsplit;             // D(m, n) of K range z at D[z dsplit + m ldd + n]
+  const float* bias;                         // + bias[n]
+  int accumulate, relu;                      // D = (D +) A B^T (+ bias), then max(., 0)
+  float* pre;                                // pre-activation (before ReLU), if not null
+  int* err;                                  // set to 1 when a bounded wait gives up
+};
+cudaError_t launch_tc_gemm(TcGemmArgs a, cudaStream_t st);
 // Viscous block Jacobi (viscpc.cu): eigenvectors / eigenvalues of every tet's spatial viscous block,
 // then z = D^-1 r (accum: z += D^-1 r) with D the tet-diagonal blocks of the viscous operator.
 stdg_status visc_pc_ensure(stdg_solver* s);
