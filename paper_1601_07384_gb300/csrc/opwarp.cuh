@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   using XIn = typename W::XIn;
   using Real = typename W::Real;
   constexpr bool kDF = W::kPlanes == 2;
+  constexpr bool kRoll = kDF && (NC == 0 || NC > 20);   // large pair kernels: rolled loops, L2 prefetch
   extern __shared__ __align__(128) unsigned char wsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   unsigned char* base = wsm + (size_t)warp * a.warp_bytes;
@@ -211,6 +212,16 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
     }
     if (__any_sync(0xffffffffu, abort)) { abort = true; break; }
     __syncwarp();
+    if (kRoll && lane == 0 && i + S * nw < a.ne) {   // the blocks after the next staged tet: towards L2
+      const int ip = i + S * nw;
+      const int4 gp = a.gface[ip];
+      const int fp[4] = {gp.x, gp.y, gp.z, gp.w};
+      bulk_prefetch_l2(static_cast<const unsigned char*>(a.Bd) + (size_t)ip * a.blk_bytes, a.blk_bytes);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fp[f] >= 0)
+          bulk_prefetch_l2(static_cast<const unsigned char*>(a.Ao) + (size_t)(fp[f] >> 1) * a.blk_bytes, a.blk_bytes);
+    }
     unsigned char* sb = base + (size_t)st * a.stage_bytes;
     XIn* xr = reinterpret_cast<XIn*>(sb + a.xraw_off);
     const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
@@ -279,25 +290,33 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
       float h0[NG], l0[NG], h1[NG], l1[NG];       // two accumulator chains per time column
 #pragma unroll
       for (int q = 0; q < NG; ++q) { h0[q] = h1[q] = 0.0f; l0[q] = l1[q] = 0.0f; }
-      for (int sl = 0; sl < 5; ++sl) {
-        if (!((pres >> sl) & 1)) continue;
+      // pair policy at N > 20 (about 200 instructions per chunk): the block and chunk loops stay rolled,
+      // as fully unrolled code outgrows the instruction cache
+      auto block_main = [&](int sl) {
+        if (!((pres >> sl) & 1)) return;
         const TB* B = blk + sl * blk_elems;
         const float* z = zb + sl * NG * NR;
         if (!((trm >> sl) & 1)) {                 // row k of the block, 4 entries per vector load
           const TB* Br = B + k * NP;
-#pragma unroll
+#pragma unroll (kRoll ? 1 : 8)
           for (int l = 0; l < NR; l += 8) {
             warp_chunk<kDF, NG>(Br + l, 1, a.plane_elems, z + l, NR, zplane, h0, l0);
             if (l + 4 < NR) warp_chunk<kDF, NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
           }
         } else {                                  // column k: A_rl = A_lr^T, one word per lane
           const TB* Bc = B + k;
-#pragma unroll
+#pragma unroll (kRoll ? 1 : 8)
           for (int l = 0; l < NR; l += 8) {
             warp_chunk<kDF, NG>(Bc + l * NP, NP, a.plane_elems, z + l, NR, zplane, h0, l0);
             if (l + 4 < NR) warp_chunk<kDF, NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
           }
         }
+      };
+      if constexpr (kRoll) {
+#pragma unroll 1
+        for (int sl = 0; sl < 5; ++sl) block_main(sl);
+      } else {
+        for (int sl = 0; sl < 5; ++sl) block_main(sl);
       }
       Real v[NG];
 #pragma unroll
@@ -319,6 +338,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
 #pragma unroll
       for (int q = 0; q < NG; ++q) { eh[q] = 0.0f; el[q] = 0.0f; }
       if (r < N) {
+#pragma unroll (kRoll ? 1 : 5)
         for (int sl = 0; sl < 5; ++sl) {
           if (!((pres >> sl) & 1)) continue;
           const TB* B = blk + sl * blk_elems;

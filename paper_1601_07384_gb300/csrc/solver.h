@@ -58,7 +58,7 @@ struct stdg_solver {
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
-  int df_min_warps = 6;                       // the pair kernel serves where this many warps fit per SM
+  int df_min_warps = 3;                       // the pair kernel serves where this many warps fit per SM
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
@@ -84,6 +84,7 @@ struct stdg_solver {
   double theta = 1.0;                          // semi-implicit pressure weight (p_t = 0 only)
   double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
   float2 *cphiP = nullptr, *cdphiP = nullptr, *cfphiP = nullptr;   // convection tables as (hi, lo) pairs
+  float2 *ctgP = nullptr, *ctwP = nullptr;                            // time basis and weights, as pairs
   // device allocations: through the caller's allocator when one was given (stdg_solver_create_alloc),
   // else cudaMalloc; released in reverse order by stdg_solver_destroy
   struct Alloc { void* p; size_t bytes; };
