@@ -300,47 +300,70 @@ def reference_arm(args, w, world, rank):
 
 
 def learned_protocol(args, g, torch):
-    """Harvest residual/error pairs from the pressure solves of the first steps, train the network
-    on the GPU, then run the next steps with FGMRES + (block Jacobi + network), FGMRES + block
-    Jacobi, and plain GMRES(50), from the same state."""
+    """The learned-preconditioner protocol (32^3 hexahedra x 6 = 196,608 tets, p = 3, p_t = 1, Beltrami
+    data, a sweep over nu in {1e-2, 3e-3, 1e-3}): for each nu, `train_steps` steps of the chosen solver
+    (KRON_MG, mixed precision) from the initial state, harvesting (residual, missed error) pairs from
+    the outer iterations of its pressure solves at evenly spaced steps; then one network (3 message-
+    passing layers, hidden 64, bfloat16 weights on the tensor cores) trained on the pairs of all three;
+    then for each nu, from the state after its training steps, `eval_steps` steps with KRON_MG and the
+    same steps with KRON_MG_GNN (every inner-solve step of the outer flexible iteration followed by a
+    step along the network's direction), with pressure iterations, s/step and fallbacks.  The time step is not given by the configuration; dt =
+    0.001 keeps the convective CFL number of the DG scheme below 1 for the 200 steps."""
     from inputs import kuhn_mesh
-    w = WORKLOADS["learned"]
-    v, t = kuhn_mesh(w["n"], seed=0)
-    mesh = g.Mesh(v, t)
-    ref = g.Reference(w["p"], w["pt"])
-    s = g.Solver(mesh, ref, w["dt"], restart=w["restart"], max_iters=20000, graph_batch=1)
-    fld = g.beltrami(np.pi / 4, np.pi / 2, w["nu"])
-    s.set_initial(fld); s.set_boundary(fld)
+    n, p, pt, dt, npic, tol = args.learned_n, 3, 1, args.learned_dt, 3, 1e-10
+    nus = [1e-2, 3e-3, 1e-3]
+    T, E = args.train_steps, args.eval_steps
+    v, t = kuhn_mesh(n, seed=0)
+    mesh, ref = g.Mesh(v, t), g.Reference(p, pt)
+    s = g.Solver(mesh, ref, dt, precision="mixed_f32")
     s.gnn_init(hidden=64, layers=3, bf16=True, seed=0)
-    s.gnn_autoharvest(nsnap=6, every=40, max_pairs=64)
-    n_train, n_eval = 3, 2
-    for _ in range(n_train):
-        s.step(w["nu"], w["npic"], method="kron_pcg", tol=w["tol"])
-    s.gnn_autoharvest(0, 0, 0)
-    t0 = time.perf_counter()
-    l0, l1 = s.gnn_train(epochs=150, lr=2e-3, batch=4)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    P0, V0, tt = s.get_state()
-    res = {}
-    for method in ["fgmres_gnn", "fgmres_bj", "gmres"]:
-        s.set_state(P0, V0, tt)
-        its, secs, fb, ok = [], [], 0, True
-        for _ in range(n_eval):
+    per_nu, marks = args.learned_pairs // len(nus), max(T // 8, 1)
+    states, t_train_steps = {}, []
+    for nu in nus:
+        fld = g.beltrami(np.pi / 4, np.pi / 2, nu)
+        s.set_initial(fld); s.set_boundary(fld)
+        got0 = None
+        for k in range(T):
+            harvest = k % marks == 0
+            s.gnn_autoharvest_mg(2 if harvest else 0, args.learned_pairs)
             torch.cuda.synchronize(); a = time.perf_counter()
-            try:
-                st = s.step(w["nu"], w["npic"], method=method, tol=w["tol"])
+            s.step(nu, npic, method="kron_mg", tol=tol)
+            torch.cuda.synchronize(); t_train_steps.append(time.perf_counter() - a)
+        s.gnn_autoharvest_mg(0, args.learned_pairs)
+        P, V, tt = s.get_state()
+        states[nu] = (P.cpu(), V.cpu(), tt)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    l0, l1 = s.gnn_train(epochs=args.learned_epochs, lr=2e-3, batch=4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - a
+    res = {}
+    for nu in nus:
+        fld = g.beltrami(np.pi / 4, np.pi / 2, nu)
+        s.set_boundary(fld)
+        res[str(nu)] = {}
+        for method in ["kron_mg", "kron_mg_gnn"]:
+            P, V, tt = states[nu]
+            s.set_state(P.cuda(), V.cuda(), tt)
+            its, secs, fb = [], [], 0
+            for _ in range(E):
+                torch.cuda.synchronize(); a = time.perf_counter()
+                st = s.step(nu, npic, method=method, tol=tol)
+                torch.cuda.synchronize(); secs.append(time.perf_counter() - a)
                 its.append(st["press_iters"]); fb += st["fallbacks"]
-            except g.StdgError as exc:
-                ok = False; its.append(str(exc)[:80])
-            torch.cuda.synchronize(); secs.append(time.perf_counter() - a)
-            if not ok:
-                break
-        res[method] = {"s_per_step": float(np.median(secs)), "press_iters": its, "converged": ok, "fallbacks": fb}
+            inner = [sum(x) for x in its]
+            res[str(nu)][method] = {"s_per_step": float(np.median(secs)), "inner_iters_per_step_mean": float(np.mean(inner)),
+                                    "press_iters_first_last": [its[0], its[-1]], "skipped_network_steps": fb}
+        b, l = res[str(nu)]["kron_mg"], res[str(nu)]["kron_mg_gnn"]
+        res[str(nu)]["iteration_ratio"] = l["inner_iters_per_step_mean"] / b["inner_iters_per_step_mean"]
+        res[str(nu)]["time_ratio"] = l["s_per_step"] / b["s_per_step"]
     print(json.dumps({"learned_preconditioner": {
-        "workload": workload_name(w), "train_steps": n_train, "eval_steps": n_eval,
-        "train_loss_first_last": [l0, l1], "train_seconds": t_train,
-        "network": "3 message-passing layers, hidden 64, bf16 weights, fp32 accumulation, added to block Jacobi",
+        "workload": f"Kuhn {n}^3 hex x 6 = {6 * n ** 3:,} tets, p={p}, p_t={pt}, Beltrami data, dt={dt}, nu in {nus}",
+        "train_steps_per_nu": T, "eval_steps_per_nu": E, "pairs": args.learned_pairs,
+        "train_loss_first_last": [l0, l1], "train_seconds": t_train, "epochs": args.learned_epochs,
+        "train_phase_s_per_step_median": float(np.median(t_train_steps)),
+        "network": "3 message-passing layers, hidden 64, bf16 weights, dense products on tcgen05 tensor cores; "
+                   "its direction taken as an extra step of the binary64 flexible outer CG of KRON_MG",
         "results": res}}))
 
 
@@ -369,9 +392,17 @@ def main():
                     help="semi-implicit pressure weight (p_t = 0 workloads only; 1 = fully implicit)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the workload's time step (labelled)")
     ap.add_argument("--learned", action="store_true",
-                    help="learned-preconditioner protocol: harvest + train on early steps, evaluate FGMRES later")
+                    help="learned-preconditioner protocol: harvest + train on early steps, evaluate later steps")
+    ap.add_argument("--learned-n", type=int, default=32, help="hexahedra per direction of the protocol's mesh")
+    ap.add_argument("--learned-dt", type=float, default=0.001)
+    ap.add_argument("--train-steps", type=int, default=100)
+    ap.add_argument("--eval-steps", type=int, default=100)
+    ap.add_argument("--learned-pairs", type=int, default=48)
+    ap.add_argument("--learned-epochs", type=int, default=200)
     ap.add_argument("--graph-batch", type=int, default=8,
                     help="Krylov iterations per captured CUDA graph (1: no graphs, e.g. for kernel-level profiling)")
+    ap.add_argument("--peak-probe", action="store_true",
+                    help="measure the binary64 / binary32 FMA throughput of the device (stdg_fma_probe) and exit")
     ap.add_argument("--op-only", type=int, default=0,
                     help="only build the workload and apply the pressure operator this many times (profiling)")
     args = ap.parse_args()
@@ -399,6 +430,13 @@ def main():
 
     if args.learned:
         return learned_protocol(args, g, torch)
+    if args.peak_probe:
+        with ClockSampler(local) as clk:
+            f64, f32 = g.fma_probe()
+        print(json.dumps({"fma_probe": {"fp64_tflops": f64, "fp32_tflops": f32,
+                                        "pair_fp64_equiv_tflops": f32 / DF_OPS_PER_TERM,
+                                        "nominal_fp64_tflops": FP64_PEAK_TFLOPS, "clocks": clk.summary()}}))
+        return
     t_setup = time.perf_counter()
     v, t = kuhn_mesh(w["n"], seed=0)
     mesh = g.Mesh(v, t)

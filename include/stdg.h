@@ -84,8 +84,18 @@ typedef enum {
  *                      preconditioned by block Jacobi plus the learned network correction
  *                      (stdg_gnn_*); later Arnoldi vectors use block Jacobi.  Needs
  *                      stdg_gnn_init.                                                      */
+/*  STDG_SOLVER_KRON_MG_GNN : STDG_SOLVER_KRON_MG in a mixed precision in which every inner-solve step
+ *                      of the binary64 flexible outer iteration is followed by a step along the learned
+ *                      network's direction z = RMS(r) net(r / RMS(r)), S-orthogonalised against the
+ *                      stored directions like any other: the error it leaves is the energy minimum over
+ *                      the enlarged search space, so the network can save inner-solve steps but never
+ *                      make a step worse; each network step costs one binary64-accurate operator
+ *                      application.  The network is trained on (residual, error) pairs from the outer
+ *                      iterations of earlier solves (stdg_gnn_autoharvest_mg).  A network step whose
+ *                      output is not finite or vanishes is skipped; stdg_solve_stats.fallback counts
+ *                      them.  stdg_solve_stats.restarts counts all outer steps.  Needs stdg_gnn_init.  */
 enum { STDG_SOLVER_GMRES = 0, STDG_SOLVER_CG = 1, STDG_SOLVER_KRON_CG = 2, STDG_SOLVER_KRON_PCG = 3,
-       STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5, STDG_SOLVER_KRON_MG = 6 };
+       STDG_SOLVER_FGMRES_BJ = 4, STDG_SOLVER_FGMRES_GNN = 5, STDG_SOLVER_KRON_MG = 6, STDG_SOLVER_KRON_MG_GNN = 7 };
 
 /* Precision of the operator blocks used inside the Krylov iteration (stdg_solver_options).
  *  STDG_PREC_FP64   : blocks and arithmetic in binary64.
@@ -402,6 +412,12 @@ stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b_dev, int nsnap, int
  * stdg_gnn_harvest(s, b, nsnap, every, max_pairs) (an extra solve per Picard iteration); nsnap = 0
  * stops harvesting. */
 stdg_status stdg_gnn_autoharvest(stdg_solver* s, int nsnap, int every, int max_pairs);
+/* While nsnap > 0, every mixed-precision coarse-corrected pressure solve (STDG_SOLVER_KRON_MG and
+ * _KRON_MG_GNN) stores nsnap pairs from its outer iterations, with no extra solve: the residual r_k of
+ * the decoupled system after k >= 1 inner-solve steps and the error x* - x_k there (x* the solve's final
+ * x).  Storage for max_pairs pairs is allocated on the first call; harvesting stops when it is full.
+ * nsnap = 0 stops harvesting. */
+stdg_status stdg_gnn_autoharvest_mg(stdg_solver* s, int nsnap, int max_pairs);
 /* `epochs` passes of Adam (learning rate lr, `batch` pairs per update) over the harvested pairs. */
 stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int batch, double* first_loss,
                            double* last_loss);
@@ -414,6 +430,13 @@ stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int batch, dou
  * if a bounded wait for the tensor cores gave up.  Allocates one word of device memory per call. */
 stdg_status stdg_tc_gemm_bf16(const float* A_dev, int64_t lda, const float* B_dev, int64_t ldb, float* D_dev,
                               int64_t ldd, int M, int N, int K, void* stream);
+
+/* Throughput of the current device's binary64 and binary32 FMA pipes in TFLOP/s (2 flops per FMA),
+ * measured with independent FMA chains on every SM and CUDA events on `stream`: the peaks the
+ * binary64 operator kernel and, divided by the 12 binary32 operations of one pair product, the
+ * pair kernel are rated against.  A measurement helper (the paper has no counterpart); allocates
+ * 16 bytes of device memory for the duration of the call. */
+stdg_status stdg_fma_probe(double* tflops_fp64, double* tflops_fp32, void* stream);
 
 /* ---------------------------------------------------------------- profiling */
 typedef struct {

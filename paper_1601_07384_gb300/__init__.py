@@ -166,6 +166,14 @@ def tc_gemm_bf16(A, B):
     return D
 
 
+def fma_probe():
+    """(binary64, binary32) FMA throughput of the current device in TFLOP/s (stdg_fma_probe)."""
+    torch = _torch()
+    a, b = C.c_double(), C.c_double()
+    _lib.check(_lib.load().stdg_fma_probe(C.byref(a), C.byref(b), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return a.value, b.value
+
+
 def tet_rule(n):
     """Collapsed Gauss-Jacobi tetrahedron rule of the library (host code)."""
     xi = np.empty((n ** 3, 3)); w = np.empty(n ** 3)
@@ -415,6 +423,10 @@ class Solver:
 
     def gnn_autoharvest(self, nsnap=8, every=50, max_pairs=64):
         _lib.check(_lib.load().stdg_gnn_autoharvest(self._h, int(nsnap), int(every), int(max_pairs)))
+
+    def gnn_autoharvest_mg(self, nsnap=8, max_pairs=64):
+        """Harvest (residual, missed error) pairs from the outer iterations of the mixed KRON_MG solves."""
+        _lib.check(_lib.load().stdg_gnn_autoharvest_mg(self._h, int(nsnap), int(max_pairs)))
 
     def gnn_train(self, epochs=50, lr=1e-3, batch=4):
         a = C.c_double(); b = C.c_double()

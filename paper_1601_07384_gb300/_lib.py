@@ -7,7 +7,8 @@ LIB_PATH = os.path.join(HERE, "libstdg.so")
 
 STATUS = {0: "STDG_OK", -1: "STDG_EINVAL", -2: "STDG_ENOMEM", -3: "STDG_ECUDA", -4: "STDG_ENOCONV",
           -5: "STDG_EMESH", -6: "STDG_ENAN", -7: "STDG_ETIMEOUT", -8: "STDG_EUNSUPPORTED"}
-SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5, "kron_mg": 6}
+SOLVER = {"gmres": 0, "cg": 1, "kron_cg": 2, "kron_pcg": 3, "fgmres_bj": 4, "fgmres_gnn": 5, "kron_mg": 6,
+          "kron_mg_gnn": 7}
 PREC = {"fp64": 0, "df32": 1, "mixed_f32": 2, "mixed_bf16": 3}
 FIELD = {"zero": 0, "constant": 1, "beltrami": 2, "curl_modes": 3}
 
@@ -101,7 +102,9 @@ SIGNATURES = {
     "stdg_gnn_harvest": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stdg_gnn_train": (C.c_int, [P, C.c_int, C.c_double, C.c_int, DP, DP]),
     "stdg_gnn_autoharvest": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
+    "stdg_gnn_autoharvest_mg": (C.c_int, [P, C.c_int, C.c_int]),
     "stdg_profile_read": (C.c_int, [P, C.POINTER(ProfileStats)]),
+    "stdg_fma_probe": (C.c_int, [DP, DP, P]),
     "stdg_tc_gemm_bf16": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P]),
     "stdg_last_error": (C.c_char_p, []),
     "stdg_version": (C.c_char_p, []),

@@ -218,6 +218,28 @@ __global__ void k_gnn_output(int64_t n, const float* __restrict__ out, const dou
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     z[e] = (add ? z[e] : 0.0) + sc * (double)out[e];
 }
+// z += s * out where the network output is finite; a non-finite output leaves z unchanged there and
+// sets *bad (the correction is then not used for that entry)
+__global__ void k_gnn_correct(int64_t n, const float* __restrict__ out, const double* __restrict__ s,
+                              double* __restrict__ z, int* bad) {
+  const double sc = s[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = sc * (double)out[e];
+    if (isfinite(v)) z[e] += v;
+    else *bad = 1;
+  }
+}
+// t = -x (- z): a harvested target before the final solution is added
+__global__ void k_neg_sum(int64_t n, const double* __restrict__ x, const double* __restrict__ z, double* __restrict__ t) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    t[e] = -(x[e] + (z ? z[e] : 0.0));
+}
+__global__ void k_sub2(int64_t n, const double* __restrict__ a, double* __restrict__ b) {   // b = a - b
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) b[e] = a[e] - b[e];
+}
+__global__ void k_axpy_d(int64_t n, double al, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) y[e] = fma(al, x[e], y[e]);
+}
 // loss terms of one pair: diff = s out - t; part0 = Sum diff^2, part1 = Sum t^2; dout = diff * s (scaled later)
 __global__ void k_gnn_lossdiff(int64_t n, const float* __restrict__ out, const double* __restrict__ s,
                                const double* __restrict__ t, float* __restrict__ dout, double* part) {
@@ -408,6 +430,39 @@ stdg_status gnn_precond(stdg_solver* s, const double* r, double* z, int use_gnn)
   return cudaGetLastError() == cudaSuccess ? STDG_OK : (set_error("preconditioner launch failed"), STDG_ECUDA);
 }
 
+// The learned correction inside the flexible outer iteration of the coarse-corrected mixed solve:
+// z += RMS(r) net(r / RMS(r)), skipping non-finite outputs (counted by the caller through *bad).
+stdg_status gnn_correct(stdg_solver* s, const double* r, double* z, int* bad) {
+  GnnState* n = s->gnn;
+  if (!n || !n->tpinv) { set_error("learned correction not initialised (stdg_gnn_init)"); return STDG_EINVAL; }
+  gnn_forward(s, r);
+  k_gnn_correct<<<kGB, 256, 0, S(s)>>>(s->ne * (int64_t)n->C, n->out, n->sdev, z, bad);
+  ++s->nlaunch;
+  return cudaGetLastError() == cudaSuccess ? STDG_OK : (set_error("learned correction launch failed"), STDG_ECUDA);
+}
+
+// Harvest from the outer iterations of the mixed solve: pair k gets R = r_k (the residual after k
+// inner-solve steps) and, first, T = -x_k (- z_k when z is given); gnn_mg_harvest_finish adds the
+// final x to every T, leaving the error x* - x_k that the network's direction should approximate.
+bool gnn_mg_harvest_room(stdg_solver* s, int k) {
+  GnnState* n = s->gnn;
+  return n && s->ah_mg > 0 && n->R && k < s->ah_mg && n->npairs + k < n->cap;
+}
+void gnn_mg_harvest_snap(stdg_solver* s, int k, const double* r, const double* x, const double* z) {
+  GnnState& n = *s->gnn;
+  const int64_t nv = s->ne * (int64_t)n.C;
+  cudaMemcpyAsync(n.R + (size_t)(n.npairs + k) * nv, r, nv * sizeof(double), cudaMemcpyDeviceToDevice, S(s));
+  k_neg_sum<<<kGB, 256, 0, S(s)>>>(nv, x, z, n.T + (size_t)(n.npairs + k) * nv);
+  ++s->nlaunch;
+}
+void gnn_mg_harvest_finish(stdg_solver* s, int got, const double* x) {
+  GnnState& n = *s->gnn;
+  const int64_t nv = s->ne * (int64_t)n.C;
+  for (int k = 0; k < got; ++k) k_axpy_d<<<kGB, 256, 0, S(s)>>>(nv, 1.0, x, n.T + (size_t)(n.npairs + k) * nv);
+  s->nlaunch += got;
+  n.npairs += got;
+}
+
 }  // namespace stdg
 
 using namespace stdg;
@@ -593,12 +648,6 @@ extern "C" stdg_status stdg_gnn_train(stdg_solver* s, int epochs, double lr, int
   return STDG_OK;
 }
 
-__global__ void k_sub2(int64_t n, const double* __restrict__ a, double* __restrict__ b) {   // b = a - b
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) b[e] = a[e] - b[e];
-}
-__global__ void k_axpy_d(int64_t n, double al, const double* __restrict__ x, double* __restrict__ y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) y[e] = fma(al, x[e], y[e]);
-}
 
 extern "C" stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b, int nsnap, int every, int max_pairs,
                                         int* total_pairs) {
@@ -640,6 +689,21 @@ extern "C" stdg_status stdg_gnn_harvest(stdg_solver* s, const double* b, int nsn
   n.npairs += got;
   if (total_pairs) *total_pairs = n.npairs;
   if (cudaStreamSynchronize(S(s)) != cudaSuccess) { set_error("stdg_gnn_harvest: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+extern "C" stdg_status stdg_gnn_autoharvest_mg(stdg_solver* s, int nsnap, int max_pairs) {
+  if (!s || !s->gnn || nsnap < 0 || (nsnap > 0 && max_pairs < 1)) { set_error("stdg_gnn_autoharvest_mg: invalid argument"); return STDG_EINVAL; }
+  cudaSetDevice(s->device);
+  GnnState& n = *s->gnn;
+  if (nsnap > 0 && !n.R) {
+    const int64_t nv = s->ne * (int64_t)n.C;
+    n.cap = max_pairs;
+    stdg_status e;
+    if ((e = dev_alloc(s, (void**)&n.R, (size_t)n.cap * nv * sizeof(double))) != STDG_OK) return e;
+    if ((e = dev_alloc(s, (void**)&n.T, (size_t)n.cap * nv * sizeof(double))) != STDG_OK) return e;
+  }
+  s->ah_mg = nsnap;
   return STDG_OK;
 }
 

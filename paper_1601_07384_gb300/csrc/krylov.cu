@@ -1100,7 +1100,7 @@ static stdg_status ensure_lowprec(stdg_solver* s) {
 // with mg, s->mix_inner_mg with block Jacobi plus the agglomeration coarse correction of mg.cu.
 // Stops when ||(I (x) Tp) r|| (the full-system residual) <= tol ||b||.
 static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, double tol, double bn, int* iters,
-                               int* outer, double* res_abs, bool mg) {
+                               int* outer, double* res_abs, bool mg, bool gnn = false, int* gnn_bad_steps = nullptr) {
   stdg_status e = ensure_lowprec(s);
   if (e == STDG_OK && mg) e = mg_ensure(s);
   if (e != STDG_OK) return e;
@@ -1150,9 +1150,29 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   GraphLoop inner;
   const bool use_graph = s->opt.graph_batch > 1;
   if (use_graph && (e = graph_capture(s, kin, body, inner)) != STDG_OK) return e;
-  int total = 0, it = 0;
+  int total = 0, it = 0, harvested = 0;
+  int* gnn_flag = reinterpret_cast<int*>(s->scal + 990);   // non-finite network output in this step
   double rfull = bn;
+  bool net_step = false;                                   // with gnn: inner-solve and network steps alternate
   while (total < s->opt.max_iters && it < 100000) {
+    if (net_step) {
+      // ---- the network's direction: z = RMS(r) net(r / RMS(r)), the flexible step along it is the
+      // energy-optimal correction in the enlarged search space; skipped (and counted) when the
+      // output is not finite or vanishes
+      net_step = false;
+      cudaMemsetAsync(z, 0, n * sizeof(double), s->stream);
+      cudaMemsetAsync(gnn_flag, 0, sizeof(int), s->stream);
+      if ((e = gnn_correct(s, r, z, gnn_flag)) != STDG_OK) return e;
+      cudaMemcpyAsync(s->hostbuf + 990, gnn_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+      const double zn = host_norm(s, z, n);               // synchronises the stream
+      if (*reinterpret_cast<const int*>(s->hostbuf + 990) != 0 || !(zn > 0.0) || !std::isfinite(zn)) {
+        if (gnn_bad_steps) ++*gnn_bad_steps;
+        continue;
+      }
+    } else {
+    net_step = gnn;
+    // harvested pairs (r_k, x* - x_k) at the start of every inner-solve step after the first
+    if (it > 0 && gnn_mg_harvest_room(s, harvested)) { gnn_mg_harvest_snap(s, harvested, r, x, nullptr); ++harvested; }
     // ---- preconditioner: kin binary32 block-Jacobi CG iterations on S d = r / ||r||, d0 = 0
     lk.f32s(s->stream, n, 1.0 / rdec, r, s->fr);
     cudaMemsetAsync(s->fx, 0, n * sizeof(float), s->stream);
@@ -1174,6 +1194,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     // z = ||r|| d in binary64
     cudaMemsetAsync(z, 0, n * sizeof(double), s->stream);
     lk.accum(s->stream, n, rdec, s->fx, z);
+    }
     // ---- flexible CG step: p = z - Sum_j (z.Q_j / P_j.Q_j) P_j over the stored directions
     const int slot = it % m, used = it < m ? it : m;
     double* p = s->fcgP + (size_t)slot * n;
@@ -1210,6 +1231,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     if (!std::isfinite(rfull)) { set_error("mixed solve: non-finite residual"); return STDG_ENAN; }
     if (rfull <= tol * bn || rdec == 0.0) break;
   }
+  if (harvested > 0) gnn_mg_harvest_finish(s, harvested, x);
   int herr = 0;
   cudaMemcpy(&herr, s->derr, sizeof(int), cudaMemcpyDeviceToHost);
   if (herr) { set_error("low-precision operator: a bounded wait timed out"); return STDG_ETIMEOUT; }
@@ -1259,6 +1281,14 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
       it += it2; rs += rs2;
       if (st) st->fallback = 1;
     }
+  } else if (method == STDG_SOLVER_KRON_MG_GNN) {
+    if (s->opt.precision != STDG_PREC_MIXED_F32 && s->opt.precision != STDG_PREC_MIXED_BF16) {
+      set_error("STDG_SOLVER_KRON_MG_GNN needs a mixed precision option"); return STDG_EINVAL;
+    }
+    if (!s->gnn) { set_error("STDG_SOLVER_KRON_MG_GNN needs stdg_gnn_init"); return STDG_EINVAL; }
+    int bad = 0;
+    r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs, true, true, &bad);
+    if (st) st->fallback = bad;
   } else if ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG || method == STDG_SOLVER_KRON_MG) &&
              (s->opt.precision == STDG_PREC_MIXED_F32 || s->opt.precision == STDG_PREC_MIXED_BF16)) {
     r = solve_mixed(s, b, x, tol, bn, &it, &rs, &rabs, method == STDG_SOLVER_KRON_MG);

@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   using XIn = typename W::XIn;
   using Real = typename W::Real;
   constexpr bool kDF = W::kPlanes == 2;
-  constexpr bool kRoll = kDF && (NC == 0 || NC > 20);   // large pair kernels: rolled loops, L2 prefetch
+  constexpr bool kRoll = kDF && (NC == 0 || NC > 20);   // large pair kernels: rolled loops
+  constexpr bool kPrefetch = kRoll;                     // there: the blocks two tets ahead go to L2 (measured
+                                                        // slower for the binary32 kernel)
   extern __shared__ __align__(128) unsigned char wsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   unsigned char* base = wsm + (size_t)warp * a.warp_bytes;
@@ -169,10 +171,9 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
       if constexpr (kDF) {
         for (int o = lane; o < Nst; o += 32) cp_async<sizeof(XIn)>(xr + sl * Nst + o, src + o);
       } else {
-        for (int o = lane; o < Nst; o += 32) {
-          const int q = o / N, l = o - q * N;
-          cp_async<sizeof(XIn)>(xr + (sl * NG + q) * NR + l, src + o);
-        }
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+          for (int l = lane; l < N; l += 32) cp_async<sizeof(XIn)>(xr + (sl * NG + q) * NR + l, src + q * N + l);
       }
     }
     cp_async_mbar_arrive_noinc(&bar[st]);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
     }
     if (__any_sync(0xffffffffu, abort)) { abort = true; break; }
     __syncwarp();
-    if (kRoll && lane == 0 && i + S * nw < a.ne) {   // the blocks after the next staged tet: towards L2
+    if (kPrefetch && lane == 0 && i + S * nw < a.ne) {   // the blocks after the next staged tet: towards L2
       const int ip = i + S * nw;
       const int4 gp = a.gface[ip];
       const int fp[4] = {gp.x, gp.y, gp.z, gp.w};

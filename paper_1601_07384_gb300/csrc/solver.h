@@ -109,6 +109,7 @@ struct stdg_solver {
   double* kzz = nullptr;                     // FGMRES preconditioned directions
   int snap_every = 0, snap_cap = 0, nsnap = 0;
   int ah_nsnap = 0, ah_every = 0, ah_max = 0;   // harvest pairs from the pressure systems of stdg_step
+  int ah_mg = 0;                                // harvest from the first ah_mg outer iterations of each mixed solve
   double* snaps = nullptr;
   // CUDA-graph batching of Krylov iterations
   cudaStream_t cstream = nullptr;
@@ -174,6 +175,10 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
 stdg_status solve_pressure_noalloc(stdg_solver* s, const double* b, double* x, double tol,
                                    stdg_solve_stats* st);
 stdg_status gnn_precond(stdg_solver* s, const double* r, double* z, int use_gnn);
+stdg_status gnn_correct(stdg_solver* s, const double* r, double* z, int* bad);
+bool gnn_mg_harvest_room(stdg_solver* s, int k);
+void gnn_mg_harvest_snap(stdg_solver* s, int k, const double* r, const double* x, const double* z);
+void gnn_mg_harvest_finish(stdg_solver* s, int got, const double* x);
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res);
 stdg_status dev_alloc(stdg_solver* s, void** p, size_t bytes);

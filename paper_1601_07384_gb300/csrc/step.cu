@@ -301,6 +301,7 @@ struct ConvArgs {
   const double *phi, *dphi, *w, *fphi, *tri_st, *tri_w, *ttau, *tw, *tg;
   FieldArg fld;
   double t0, dt;
+  const float2 *tgP, *twP;   // the time basis at the time points [nt][Ng] and the time weights, as pairs
   const int* bidx;      // compact boundary index per face (points of host-callback data)
   int bnpt;             // data points per boundary face: (nq + nqf) * nt, face points after nq * nt
   const double* vbar;   // [3][ne][Nst]
@@ -338,6 +339,50 @@ __device__ __forceinline__ void pair_fma(float2 a, float2 b, float& s, float& c)
   s = s2;
 }
 __device__ __forceinline__ double pair_value(float s, float c) { return (double)s + (double)c; }
+// (s, c) with |c| small against |s| -> a normalised pair (hi, lo), hi = fl32(s + c) (Fast2Sum)
+__device__ __forceinline__ float2 pair_norm(float s, float c) {
+  const float h = s + c;
+  return make_float2(h, c - (h - s));
+}
+// the product of two pairs as a normalised pair: the high parts' product exactly (FMA), the cross terms
+// into its error
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
+  return pair_norm(p, e);
+}
+// a + b and a - b of pairs (TwoSum of the high parts, low parts added to its error)
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+  return pair_norm(s, e);
+}
+__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// S[c][b] = Sum_k phi_k(x_q) V[c][b][k] at one quadrature point, as normalised pairs: each basis value
+// is loaded once and used by the 3 Ng sums (the coefficients V are the same for every point: shared
+// memory broadcasts)
+__device__ __forceinline__ void contract_point(const float2* __restrict__ ph, const float2* V, int N, int Ng, int Nst,
+                                               float2 (&S)[3][kMaxNg]) {
+  float ss[3][kMaxNg], cc[3][kMaxNg];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < kMaxNg; ++b) { ss[c][b] = 0.0f; cc[c][b] = 0.0f; }
+  for (int k = 0; k < N; ++k) {
+    const float2 pk = ph[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < kMaxNg; ++b)
+        if (b < Ng) pair_fma(pk, V[c * Nst + b * N + k], ss[c][b], cc[c][b]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < kMaxNg; ++b) S[c][b] = pair_norm(ss[c][b], cc[c][b]);
+}
 
 __global__ void k_split_pairs(int64_t n, const double* __restrict__ in, float2* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -363,46 +408,58 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2
     ViP[o] = pair_split(a.vbar[((size_t)c * ne + i) * Nst + rem]);
   }
   __syncthreads();
-  // volume term: - int grad(phi~_k) . F_c(vbar)
+  // volume term: - int grad(phi~_k) . F_c(vbar); the flux and its time folding in binary32 pairs
+  // (the FP64 pipe, 1/64 of the FP32 rate on sm_103a, stays free of the per-point work)
+  __shared__ float2 JiP[9];
+  if (threadIdx.x < 9) JiP[threadIdx.x] = pair_split(Ji[threadIdx.x]);
+  __syncthreads();
   for (int base = 0; base < a.nq; base += kConvCH) {
     const int cnt = min(kConvCH, a.nq - base);
     if (u < cnt) {
       const int q = base + u;
       const float2* ph = phiP + (size_t)q * N;
-      double S[3][kMaxNg];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < kMaxNg; ++b) {
-          float ss = 0.0f, cc = 0.0f;
-          if (b < Ng)
-            for (int k = 0; k < N; ++k) pair_fma(ph[k], ViP[c * Nst + b * N + k], ss, cc);
-          S[c][b] = pair_value(ss, cc);
-        }
-      double* Gu = G + (size_t)u * 9 * Ng;
-      for (int e = 0; e < 9 * Ng; ++e) Gu[e] = 0.0;
-      const double wq = a.dt * dj * a.w[q];
+      float2 SP[3][kMaxNg];
+      contract_point(ph, ViP, N, Ng, Nst, SP);
+      float2* Gu = GP + (size_t)u * 9 * Ng;       // accumulators (s, c) of G[c][e][ta]
+      for (int e = 0; e < 9 * Ng; ++e) Gu[e] = make_float2(0.0f, 0.0f);
+      const float2 wqP = pair_split(a.dt * dj * a.w[q]);
       for (int ti = 0; ti < nt; ++ti) {
-        const double* g = a.tg + ti * Ng;
-        double v[3];
+        const float2* g = a.tgP + ti * Ng;
+        float2 vP[3], uP[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          double s = 0.0;
+          float ss = 0.0f, cc = 0.0f;
 #pragma unroll
           for (int b = 0; b < kMaxNg; ++b)
-            if (b < Ng) s = fma(g[b], S[c][b], s);
-          v[c] = s;
+            if (b < Ng) pair_fma(g[b], SP[c][b], ss, cc);
+          vP[c] = pair_norm(ss, cc);
         }
-        const double W = wq * a.tw[ti];
-        // H[c][e] = W v_c Sum_d Jinv[e][d] v_d  (grad_x phi = Sum_e Jinv[e][d] d_e phi)
-        for (int c = 0; c < 3; ++c)
+        // u = Jinv v: grad_x phi = Sum_e Jinv[e][d] d_e phi
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          float ss = 0.0f, cc = 0.0f;
+          pair_fma(JiP[3 * e], vP[0], ss, cc);
+          pair_fma(JiP[3 * e + 1], vP[1], ss, cc);
+          pair_fma(JiP[3 * e + 2], vP[2], ss, cc);
+          uP[e] = pair_norm(ss, cc);
+        }
+        const float2 W = pair_mul(wqP, a.twP[ti]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 Wv = pair_mul(W, vP[c]);
+#pragma unroll
           for (int e = 0; e < 3; ++e) {
-            const double h = W * v[c] * (Ji[3 * e] * v[0] + Ji[3 * e + 1] * v[1] + Ji[3 * e + 2] * v[2]);
-            for (int ta = 0; ta < Ng; ++ta) Gu[(c * 3 + e) * Ng + ta] = fma(g[ta], h, Gu[(c * 3 + e) * Ng + ta]);
+            const float2 h = pair_mul(Wv, uP[e]);     // H[c][e] = W v_c u_e
+            float2* Gce = Gu + (c * 3 + e) * Ng;
+            for (int ta = 0; ta < Ng; ++ta) {
+              float2 G = Gce[ta];
+              pair_fma(g[ta], h, G.x, G.y);
+              Gce[ta] = G;
+            }
           }
+        }
       }
-      float2* GPu = GP + (size_t)u * 9 * Ng;
-      for (int e = 0; e < 9 * Ng; ++e) GPu[e] = pair_split(Gu[e]);
+      for (int e = 0; e < 9 * Ng; ++e) Gu[e] = pair_norm(Gu[e].x, Gu[e].y);
     }
     __syncthreads();
     for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
@@ -427,7 +484,8 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2
     const int code = a.t2code[4 * i + f];
     const int codeb = nb >= 0 ? (me_left ? a.code_r[j] : a.code_l[j]) : 0;
     const double sg = me_left ? 1.0 : -1.0;
-    const double n0 = sg * a.normal[3 * j], n1 = sg * a.normal[3 * j + 1], n2 = sg * a.normal[3 * j + 2];
+    const float2 nP[3] = {pair_split(sg * a.normal[3 * j]), pair_split(sg * a.normal[3 * j + 1]),
+                          pair_split(sg * a.normal[3 * j + 2])};
     const double* fv = a.fvx + 9 * (size_t)j;
     if (nb >= 0) {
       for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
@@ -441,71 +499,72 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2
       if (u < cnt) {
         const int q = base + u;
         const float2* ph = fphiP + ((size_t)code * a.nqf + q) * N;
-        double Sm[3][kMaxNg], Sp[3][kMaxNg];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int b = 0; b < kMaxNg; ++b) {
-            float ss = 0.0f, cc = 0.0f;
-            if (b < Ng)
-              for (int k = 0; k < N; ++k) pair_fma(ph[k], ViP[c * Nst + b * N + k], ss, cc);
-            Sm[c][b] = pair_value(ss, cc);
-          }
+        float2 SmP[3][kMaxNg], SpP[3][kMaxNg];
+        contract_point(ph, ViP, N, Ng, Nst, SmP);
         double x[3] = {0.0, 0.0, 0.0};
         if (nb >= 0) {
-          const float2* phn = fphiP + ((size_t)codeb * a.nqf + q) * N;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int b = 0; b < kMaxNg; ++b) {
-              float ss = 0.0f, cc = 0.0f;
-              if (b < Ng)
-                for (int k = 0; k < N; ++k) pair_fma(phn[k], VnP[c * Nst + b * N + k], ss, cc);
-              Sp[c][b] = pair_value(ss, cc);
-            }
+          contract_point(fphiP + ((size_t)codeb * a.nqf + q) * N, VnP, N, Ng, Nst, SpP);
         } else {
           const double s = a.tri_st[2 * q], t = a.tri_st[2 * q + 1];
           for (int d = 0; d < 3; ++d) x[d] = fv[d] + s * (fv[3 + d] - fv[d]) + t * (fv[6 + d] - fv[d]);
         }
-        double* Gu = G + (size_t)u * 3 * Ng;
-        for (int e = 0; e < 3 * Ng; ++e) Gu[e] = 0.0;
-        const double wq = a.dt * 2.0 * a.area[j] * a.tri_w[q];
+        float2* Gu = GP + (size_t)u * 3 * Ng;     // accumulators (s, c) of G[c][ta]
+        for (int e = 0; e < 3 * Ng; ++e) Gu[e] = make_float2(0.0f, 0.0f);
+        const float2 wqP = pair_split(a.dt * 2.0 * a.area[j] * a.tri_w[q]);
         for (int ti = 0; ti < nt; ++ti) {
-          const double* g = a.tg + ti * Ng;
-          double vm[3], vp[3];
+          const float2* g = a.tgP + ti * Ng;
+          float2 vm[3], vp[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            double s = 0.0;
+            float ss = 0.0f, cc = 0.0f;
 #pragma unroll
             for (int b = 0; b < kMaxNg; ++b)
-              if (b < Ng) s = fma(g[b], Sm[c][b], s);
-            vm[c] = s;
+              if (b < Ng) pair_fma(g[b], SmP[c][b], ss, cc);
+            vm[c] = pair_norm(ss, cc);
           }
           if (nb >= 0) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              double s = 0.0;
+              float ss = 0.0f, cc = 0.0f;
 #pragma unroll
               for (int b = 0; b < kMaxNg; ++b)
-                if (b < Ng) s = fma(g[b], Sp[c][b], s);
-              vp[c] = s;
+                if (b < Ng) pair_fma(g[b], SpP[c][b], ss, cc);
+              vp[c] = pair_norm(ss, cc);
             }
           } else {
+            double vb[3];
             eval_field(a.fld, x, a.t0 + a.ttau[ti] * a.dt,
-                       (int64_t)a.bidx[j] * a.bnpt + (int64_t)a.nq * nt + (int64_t)q * nt + ti, a.ttau[ti], vp);
+                       (int64_t)a.bidx[j] * a.bnpt + (int64_t)a.nq * nt + (int64_t)q * nt + ti, a.ttau[ti], vb);
+            for (int c = 0; c < 3; ++c) vp[c] = pair_split(vb[c]);
           }
-          const double unm = vm[0] * n0 + vm[1] * n1 + vm[2] * n2;
-          const double unp = vp[0] * n0 + vp[1] * n1 + vp[2] * n2;
-          const double smax = 2.0 * fmax(sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]),
-                                         sqrt(vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]));
-          const double W = wq * a.tw[ti];
+          // Rusanov flux, s_max = 2 max(|v+|, |v-|) pointwise (the square roots in binary64)
+          float s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f, s3 = 0.0f, c3 = 0.0f, s4 = 0.0f, c4 = 0.0f;
+#pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const double h = W * (0.5 * (vp[c] * unp + vm[c] * unm) - 0.5 * smax * (vp[c] - vm[c]));
-            for (int ta = 0; ta < Ng; ++ta) Gu[c * Ng + ta] = fma(g[ta], h, Gu[c * Ng + ta]);
+            pair_fma(vm[c], nP[c], s1, c1);
+            pair_fma(vp[c], nP[c], s2, c2);
+            pair_fma(vm[c], vm[c], s3, c3);
+            pair_fma(vp[c], vp[c], s4, c4);
+          }
+          const float2 unm = pair_norm(s1, c1), unp = pair_norm(s2, c2);
+          const double smax = 2.0 * fmax(sqrt(pair_value(s4, c4)), sqrt(pair_value(s3, c3)));
+          const float2 W = pair_mul(wqP, a.twP[ti]);
+          const float2 hs = pair_mul(W, pair_split(0.5 * smax));
+          const float2 Wh = pair_mul(W, make_float2(0.5f, 0.0f));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            // h = W (0.5 (v+_c un+ + v-_c un-) - 0.5 s_max (v+_c - v-_c))
+            const float2 cen = pair_mul(Wh, pair_add(pair_mul(vp[c], unp), pair_mul(vm[c], unm)));
+            const float2 h = pair_add(cen, pair_neg(pair_mul(hs, pair_add(vp[c], pair_neg(vm[c])))));
+            float2* Gc = Gu + c * Ng;
+            for (int ta = 0; ta < Ng; ++ta) {
+              float2 G = Gc[ta];
+              pair_fma(g[ta], h, G.x, G.y);
+              Gc[ta] = G;
+            }
           }
         }
-        float2* GPu = GP + (size_t)u * 3 * Ng;
-        for (int e = 0; e < 3 * Ng; ++e) GPu[e] = pair_split(Gu[e]);
+        for (int e = 0; e < 3 * Ng; ++e) Gu[e] = pair_norm(Gu[e].x, Gu[e].y);
       }
       __syncthreads();
       for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
@@ -831,13 +890,18 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
   if (!s->cphiP) {                                  // the convection tables as binary32 pairs, once
     const size_t n1 = (size_t)s->nq_nl * N, n2 = (size_t)s->nq_nl * 3 * N, n3 = (size_t)64 * s->nqf_nl * N;
-    if ((e = dev_alloc(s, (void**)&s->cphiP, (n1 + n2 + n3) * sizeof(float2))) != STDG_OK) return e;
+    const size_t n4 = (size_t)s->nt_nl * Ng, n5 = (size_t)s->nt_nl;
+    if ((e = dev_alloc(s, (void**)&s->cphiP, (n1 + n2 + n3 + n4 + n5) * sizeof(float2))) != STDG_OK) return e;
     s->cdphiP = s->cphiP + n1;
     s->cfphiP = s->cdphiP + n2;
-    s->nlaunch += 3;
+    s->ctgP = s->cfphiP + n3;
+    s->ctwP = s->ctgP + n4;
+    s->nlaunch += 5;
     k_split_pairs<<<256, 256, 0, st>>>((int64_t)n1, s->dr.tet_nl_phi, s->cphiP);
     k_split_pairs<<<256, 256, 0, st>>>((int64_t)n2, s->dr.tet_nl_dphi, s->cdphiP);
     k_split_pairs<<<256, 256, 0, st>>>((int64_t)n3, s->dr.face_nl_phi, s->cfphiP);
+    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n4, s->d_tg, s->ctgP);
+    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n5, s->d_tw, s->ctwP);
   }
   phase_mark(s, 0);
   for (int k = 0; k < n_picard; ++k) {
@@ -860,7 +924,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
                 s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
                 s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
-                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, bc_arg(s), s->t, s->dt, s->bidx,
+                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, bc_arg(s), s->t, s->dt, s->ctgP, s->ctwP, s->bidx,
                 (s->nq_nl + s->nqf_nl) * s->nt_nl, s->Vbar, s->Ups};
     ++s->nlaunch;
     k_convection<<<ne, kConvCH, conv_smem, st>>>(ca, s->cphiP, s->cdphiP, s->cfphiP);

@@ -165,7 +165,8 @@ def test_agglomerates_of_a_kuhn_mesh(lib, n):
 
 def test_periodic_mesh_matches_oracle(lib):
     """stdg_mesh_create_periodic: the same face table as the oracle's periodic mesh (every face
-    interior), and a solver refuses it with STDG_EUNSUPPORTED before touching a device."""
+    interior), and without a GPU the solver creation fails with STDG_ECUDA (no host path); on a
+    GPU it is accepted."""
     import ctypes as C
     import paper_1601_07384_gb300 as g
     from paper_1601_07384_gb300 import _lib
@@ -180,6 +181,15 @@ def test_periodic_mesh_matches_oracle(lib):
     assert np.array_equal(lf, om.fl) and np.array_equal(rf, om.fr)
     h = C.c_void_p()
     st = _lib.load().stdg_solver_create(gm._h, g.Reference(1, 0)._h, 0.01, None, None, C.byref(h))
-    assert st == -8                                 # STDG_EUNSUPPORTED
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        assert st == -3                             # STDG_ECUDA
+    else:
+        assert st == 0
+        _lib.load().stdg_solver_destroy(h)
     with pytest.raises(g.StdgError):
         g.Mesh(v, t, period=[0.0, 1.0, 1.0])
