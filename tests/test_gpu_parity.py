@@ -269,13 +269,44 @@ def test_largest_mesh_sampled_rows():
     rows = np.concatenate([[0, om.ne - 1], np.random.default_rng(22).choice(om.ne, 6, replace=False)])
     expect = _oracle_rows(om, d, x, rows)
     xd = torch.from_numpy(x.ravel()).cuda()
-    for prec in ("fp64", "df32"):
+    for prec, tol in (("fp64", 1e-12), ("df32", 1e-12), ("mixed_f32", 4e-6)):
         gs = g.Solver(g.Mesh(v, t), g.Reference(4, 4), 0.01, precision=prec)
-        y = gs.pressure_apply(xd, pinned=False).cpu().numpy().reshape(om.ne, d.Nst)
+        if prec == "mixed_f32":       # the binary32 kernel of the inner iterations (N = 35: split rows)
+            y = gs.pressure_apply_f32(xd.float(), pinned=False).double().cpu().numpy().reshape(om.ne, d.Nst)
+        else:
+            y = gs.pressure_apply(xd, pinned=False).cpu().numpy().reshape(om.ne, d.Nst)
         for i, yi in zip(rows, expect):
-            assert rel(y[i], yi) <= 1e-12, (prec, i)
+            assert rel(y[i], yi) <= tol, (prec, i)
         del gs
         torch.cuda.empty_cache()
+
+
+def test_largest_configuration_step_properties():
+    """One time step of the largest configuration as the benchmark runs it (40^3 x 6 = 384,000 tets,
+    p = p_t = 4, the solenoidal field with no-slip walls, nu = 1e-3, dt = 0.01, 3 Picard iterations,
+    KRON_MG in mixed precision to 1e-10), checked through properties that hold at any size: every
+    pressure solve's true residual (binary64 operator) meets the tolerance, the discrete divergence
+    (Eq. CS_15) of the new velocity vanishes to rounding against the velocity's size, the state is
+    finite and the kinetic-energy proxy does not grow (no forcing, walls at rest)."""
+    import paper_1601_07384_gb300 as g
+    from inputs import SolenoidalModes
+    v, t = kuhn_mesh(40, seed=0)
+    gs = g.Solver(g.Mesh(v, t), g.Reference(4, 4), 0.01, precision="mixed_f32")
+    sm = SolenoidalModes(seed=1)
+    gs.set_initial(g.curl_modes(sm.k, sm.a, sm.phi, sm.scale))
+    gs.set_boundary(g.zero())
+    _, V0, _ = gs.get_state()
+    e0 = float(torch.linalg.norm(V0))
+    st = gs.step(1e-3, 3, method="kron_mg", tol=1e-10)
+    P, V, tt = gs.get_state()
+    assert abs(tt - 0.01) < 1e-15
+    assert max(st["press_residual"]) <= 1e-10
+    assert torch.isfinite(P).all() and torch.isfinite(V).all()
+    vmax = float(V.abs().max())
+    assert st["max_divergence"] <= 1e-12 * vmax
+    assert float(torch.linalg.norm(V)) <= 1.001 * e0
+    del gs
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("n,p,pt", [(3, 1, 0), (2, 2, 1), (2, 3, 1), (2, 4, 2)])
