@@ -541,9 +541,11 @@ static bool df_serves(const stdg_solver* s, const ApplyArgs& a) {
   return s->wdBv && a.Bextra == s->Bvisc && a.extra_coef == -1.0 && a.tacc_identity && !a.pinned;
 }
 
-static stdg_status op_apply(stdg_solver* s, const ApplyArgs& a, const double* x, double* y) {
+// y = op x with the binary64-accurate kernel for this operator (the pair kernel where it serves,
+// else the binary64 kernel), or with the binary64 kernel alone when fp64_only
+static stdg_status op_apply(stdg_solver* s, const ApplyArgs& a, const double* x, double* y, bool fp64_only = false) {
   const bool prof = s->prof && !s->ev.empty() && !s->capturing;
-  const bool use_df = df_serves(s, a);
+  const bool use_df = !fp64_only && df_serves(s, a);
   if (prof) {
     if (2 * s->ev_used >= (int)s->ev.size()) prof_fold(s);
     s->ev_kind[s->ev_used] = use_df ? 1 : 0;
@@ -1150,7 +1152,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
   GraphLoop inner;
   const bool use_graph = s->opt.graph_batch > 1;
   if (use_graph && (e = graph_capture(s, kin, body, inner)) != STDG_OK) return e;
-  int total = 0, it = 0, harvested = 0;
+  int total = 0, it = 0, ring = 0, refresh = 0, harvested = 0;
   int* gnn_flag = reinterpret_cast<int*>(s->scal + 990);   // non-finite network output in this step
   double rfull = bn;
   bool net_step = false;                                   // with gnn: inner-solve and network steps alternate
@@ -1196,7 +1198,7 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     lk.accum(s->stream, n, rdec, s->fx, z);
     }
     // ---- flexible CG step: p = z - Sum_j (z.Q_j / P_j.Q_j) P_j over the stored directions
-    const int slot = it % m, used = it < m ? it : m;
+    const int slot = ring % m, used = ring < m ? ring : m;
     double* p = s->fcgP + (size_t)slot * n;
     double* q = s->fcgQ + (size_t)slot * n;
     if (used == 0) {
@@ -1223,13 +1225,27 @@ static stdg_status solve_mixed(stdg_solver* s, const double* b, double* x, doubl
     cudaMemcpyAsync(s->hostbuf + 880, o_rr, (Ng + 1) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     s->nlaunch += 9;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("mixed solve: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
-    ++it;
+    ++it; ++ring;
     double rr = 0.0;
     for (int a = 0; a < Ng; ++a) rr += s->hostbuf[880 + a];
     rdec = std::sqrt(rr);
     rfull = std::sqrt(s->hostbuf[880 + Ng]);
     if (!std::isfinite(rfull)) { set_error("mixed solve: non-finite residual"); return STDG_ENAN; }
-    if (rfull <= tol * bn || rdec == 0.0) break;
+    if (rfull <= tol * bn || rdec == 0.0) {
+      // the recurrence says converged: evaluate b - A x with the binary64 kernel (the pair kernel's
+      // rounding, ~1e-14 of |A| |x|, can exceed tol |b|); if it misses the tolerance, continue from
+      // that residual with a fresh set of directions (at most 3 times)
+      if ((e = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, s->kq, true)) != STDG_OK) return e;
+      k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);   // kq = b - A x
+      ++s->nlaunch;
+      rfull = host_norm(s, s->kq, n);
+      if (rfull <= tol * bn || rdec == 0.0 || refresh >= 3) break;
+      ++refresh;
+      k_timemix<<<kRedBlocks, kRedThreads, 0, s->stream>>>(s->ne, N, Ng, Tpinv, -1.0, s->kq, r);   // r = -(I (x) Tp^-1)(b - A x)
+      ++s->nlaunch;
+      rdec = host_norm(s, r, n);
+      ring = 0;
+    }
   }
   if (harvested > 0) gnn_mg_harvest_finish(s, harvested, x);
   int herr = 0;
@@ -1309,14 +1325,22 @@ stdg_status solve_pressure(stdg_solver* s, const double* b, double* x, double to
   }
   if (r != STDG_OK && r != STDG_ENOCONV) return r;
   if (st) {
-    // report the residual of the full pinned system for every method
-    stdg_status e2 = apply_pressure(s, x, s->kq, 1, 0, 1.0, -1.0);
-    if (e2 != STDG_OK) return e2;
-    ++s->nlaunch;
-    k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);
+    // report the residual of the full pinned system for every method, evaluated with the binary64
+    // kernel (the mixed solves have just done so for their final x)
+    const bool mixed_done = r == STDG_OK && bn > 0.0 &&
+        (method == STDG_SOLVER_KRON_MG_GNN || ((method == STDG_SOLVER_KRON_CG || method == STDG_SOLVER_KRON_PCG ||
+          method == STDG_SOLVER_KRON_MG) && (s->opt.precision == STDG_PREC_MIXED_F32 || s->opt.precision == STDG_PREC_MIXED_BF16)));
+    double rn = rabs;
+    if (!mixed_done && bn > 0.0) {
+      stdg_status e2 = op_apply(s, pressure_op(s, 1, 0, 1.0, -1.0), x, s->kq, true);
+      if (e2 != STDG_OK) return e2;
+      ++s->nlaunch;
+      k_scale_copy<<<kRedBlocks, kRedThreads, 0, s->stream>>>(n, b, nullptr, 1, s->kq);
+      rn = host_norm(s, s->kq, n);
+    }
     st->iterations = it;
     st->restarts = rs;
-    st->rel_residual = bn > 0 ? host_norm(s, s->kq, n) / bn : 0.0;
+    st->rel_residual = bn > 0 ? rn / bn : 0.0;
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return r;
@@ -1644,6 +1668,98 @@ static stdg_status cocg_viscous(stdg_solver* s, const ApplyArgs& a, double nu, c
   return STDG_OK;
 }
 
+// Inner solve of the mixed-precision viscous refinement: x += A^-1 b to tol_abs (the decoupled
+// residual norm), all vectors binary32 (the solver's binary32 work vectors, free between pressure
+// solves), operator from the binary32 viscous blocks, multipliers and cross products restricted to
+// the tridiagonal entries the block-diagonal time matrix R can couple (cocg32.cu).  b and x are
+// binary64; x is left unchanged unless the solve reaches tol_abs.
+static stdg_status cocg_viscous32(stdg_solver* s, const ApplyArgs& a, double nu, const double* b, double* x,
+                                  double tol_abs, int* iters, double* res) {
+  const int Ng = s->Ng, N = s->N, ne = (int)s->ne;
+  const int64_t n = s->ne * (int64_t)s->Nst;
+  if (s->vbd < 0) s->vbd = time_blockdiag(s->K.data(), Ng, s->vW, s->vWinv, s->vR, s->vpair) ? 1 : 0;
+  if (!s->vbd) return STDG_EUNSUPPORTED;
+  stdg_status e = visc_pc_ensure(s);
+  if (e == STDG_OK) e = ensure_lowprec(s);
+  if (e != STDG_OK) return e;
+  cudaError_t ce = warp_prepare_f32_visc(s);
+  if (ce != cudaSuccess) { set_error("binary32 viscous blocks: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  Mix32 W{}, Wi{};
+  PairArg pr{};
+  for (int q = 0; q < Ng * Ng; ++q) { W.v[q] = (float)s->vW[q]; Wi.v[q] = (float)s->vWinv[q]; }
+  for (int c = 0; c < Ng; ++c) pr.p[c] = s->vpair[c];
+  ApplyArgs at = a;                                   // the decoupled operator: time matrix R
+  for (int q = 0; q < Ng * Ng; ++q) at.Kmass[q] = s->vR[q];
+  float* y = s->fx; float* r = s->fr; float* z = s->fz; float* p = s->fp; float* q = s->fq;
+  double* C = s->scal + 300;                          // Ng^2 cross products
+  double* rho = s->scal + 330;                        // 2 Ng
+  double* Ma = s->scal + 340; double* Mb = s->scal + 370;   // Ng^2 each
+  double* flag = s->scal + 398; double* resd = s->scal + 399;
+  const int G2 = Ng * Ng;
+  c32_mix_to32(s->stream, ne, N, Ng, Wi, b, r);      // r = (I (x) W^-1) b, y = 0
+  cudaMemsetAsync(y, 0, n * sizeof(float), s->stream);
+  if ((e = visc_pc_apply32(s, nu, r, z, s->vR)) != STDG_OK) return e;
+  cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+  cudaMemsetAsync(flag, 0, sizeof(double), s->stream);
+  c32_cross(s->stream, ne, N, Ng, r, z, s->part);
+  k_final<<<G2, kRedThreads, 0, s->stream>>>(kRedBlocks, G2, s->part, C);
+  k_cocg_scalars<<<1, 32, 0, s->stream>>>(Ng, pr, 2, C, rho, Ma, flag);
+  s->nlaunch += 4;
+  const int B = s->opt.graph_batch > 1 ? std::min(4, s->opt.graph_batch) : 1;
+  auto body = [&](int slot, cudaEvent_t* evs) -> stdg_status {
+    if (evs) cudaEventRecordWithFlags(evs[0], s->stream, cudaEventRecordExternal);
+    const cudaError_t ae = warp_launch_f32_visc(s, p, q, at.scale, at.mass_coef, at.Kmass);
+    if (evs) cudaEventRecordWithFlags(evs[1], s->stream, cudaEventRecordExternal);
+    if (ae != cudaSuccess) { set_error("binary32 viscous operator: %s", cudaGetErrorString(ae)); return STDG_ECUDA; }
+    const int want = slot == B - 1;
+    c32_cross(s->stream, ne, N, Ng, p, q, s->part);
+    k_final<<<G2, kRedThreads, 0, s->stream>>>(kRedBlocks, G2, s->part, C);
+    k_cocg_scalars<<<1, 32, 0, s->stream>>>(Ng, pr, 0, C, rho, Ma, flag);
+    c32_update(s->stream, ne, N, Ng, Ma, y, r, p, q, W, s->part, want);
+    if (want) {
+      k_final_norm<<<1, kRedThreads, 0, s->stream>>>(kRedBlocks, s->part, resd);
+      cudaMemcpyAsync(s->hostbuf + slot, resd, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    }
+    stdg_status e2 = visc_pc_apply32(s, nu, r, z, s->vR);
+    if (e2 != STDG_OK) return e2;
+    c32_cross(s->stream, ne, N, Ng, r, z, s->part);
+    k_final<<<G2, kRedThreads, 0, s->stream>>>(kRedBlocks, G2, s->part, C);
+    k_cocg_scalars<<<1, 32, 0, s->stream>>>(Ng, pr, 1, C, rho, Mb, flag);
+    c32_dir(s->stream, ne, N, Ng, Mb, z, p);
+    return STDG_OK;
+  };
+  int it = 0;
+  double rabs = INFINITY;
+  constexpr int kpi = 10;                             // kernels per iteration (+1 norm per check)
+  if (B > 1) {
+    e = run_batched(s, B, kpi, s->opt.max_iters, tol_abs, body, &it, &rabs, 2, true);
+    s->nlaunch += it / B;
+  } else {
+    e = STDG_OK;
+    while (it < s->opt.max_iters) {
+      if ((e = body(0, nullptr)) != STDG_OK) break;
+      s->nlaunch += kpi + 1;
+      ++s->op_launches;
+      ++it;
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("viscous COCG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+      rabs = s->hostbuf[0];
+      if (!std::isfinite(rabs)) { set_error("Krylov: non-finite residual"); e = STDG_ENAN; break; }
+      if (rabs <= tol_abs) break;
+    }
+  }
+  double hflag = 0.0;
+  cudaMemcpyAsync(&hflag, flag, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { set_error("viscous COCG: %s", cudaGetErrorString(cudaGetLastError())); return STDG_ECUDA; }
+  *iters = it;
+  *res = rabs;
+  if (e != STDG_OK) return e;
+  if (hflag != 0.0) { set_error("viscous COCG: breakdown (p^T A p = 0)"); return STDG_ENOCONV; }
+  if (!(rabs <= tol_abs)) { set_error("viscous COCG reached max_iters (%d)", it); return STDG_ENOCONV; }
+  ++s->nlaunch;
+  c32_mix_acc64(s->stream, ne, N, Ng, W, y, x);     // x += (I (x) W) y
+  return STDG_OK;
+}
+
 stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu, double tol, int* iters,
                           double* res) {
   ApplyArgs a{};
@@ -1676,10 +1792,9 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
     // mixed precision: binary64 refinement around binary32 inner COCG solves.  Each outer step forms
     // the true residual r = b - A x with the binary64-accurate operator and solves A d = r with the
     // binary32 operator to 1e-5 ||r|| (its rounding limits how far an inner solve can go), x += d.
-    stdg_status e0 = ensure_basis(s, 2);
+    stdg_status e0 = ensure_basis(s, s->visc_inner64 ? 2 : 1);
     if (e0 != STDG_OK) return e0;
     double* ro = s->basis;
-    double* d = s->basis + (size_t)s->ne * s->Nst;
     const int64_t nn = s->ne * (int64_t)s->Nst;
     for (int outer = 0; outer < 8; ++outer) {
       if ((e0 = op_apply(s, a, x, ro)) != STDG_OK) return e0;
@@ -1690,12 +1805,16 @@ stdg_status solve_viscous(stdg_solver* s, const double* b, double* x, double nu,
       if (nr <= tol * bn) { *iters = it1; *res = nr; return STDG_OK; }
       int itk = 0;
       double rk = 0.0;
-      e0 = cocg_viscous(s, a, nu, ro, d, std::max(1e-5 * nr, 0.5 * tol * bn), &itk, &rk, true, true);
+      e0 = s->visc_inner64 ? cocg_viscous(s, a, nu, ro, s->basis + nn, std::max(1e-5 * nr, 0.5 * tol * bn), &itk, &rk,
+                                          true, true)
+                           : cocg_viscous32(s, a, nu, ro, x, std::max(1e-5 * nr, 0.5 * tol * bn), &itk, &rk);
       it1 += itk;
       if (e0 == STDG_EUNSUPPORTED || e0 == STDG_ENOCONV) break;   // binary64 solvers below
       if (e0 != STDG_OK) return e0;
-      ++s->nlaunch;
-      k_add<<<kRedBlocks, kRedThreads, 0, s->stream>>>(nn, d, x);
+      if (s->visc_inner64) {
+        ++s->nlaunch;
+        k_add<<<kRedBlocks, kRedThreads, 0, s->stream>>>(nn, s->basis + nn, x);
+      }
     }
   }
   if (use_cocg) {
