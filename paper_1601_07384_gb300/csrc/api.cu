@@ -85,6 +85,8 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
     if (mm && std::atoi(mm) > 0 && std::atoi(mm) <= 16) s->mix_m = std::atoi(mm);
     const char* dw = std::getenv("STDG_DF_MIN_WARPS");  // pair kernel used when this many warps fit per SM
     if (dw && std::atoi(dw) > 0 && std::atoi(dw) <= 64) s->df_min_warps = std::atoi(dw);
+    const char* vi = std::getenv("STDG_VISC_INNER64");
+    s->visc_inner64 = vi && std::atoi(vi) == 1;
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;

@@ -59,6 +59,7 @@ struct stdg_solver {
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
   int df_min_warps = 3;                       // the pair kernel serves where this many warps fit per SM
+  bool visc_inner64 = false;                  // mixed viscous refinement: binary64-vector inner COCG
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32
@@ -212,6 +213,18 @@ cudaError_t launch_tc_gemm(TcGemmArgs a, cudaStream_t st);
 stdg_status visc_pc_ensure(stdg_solver* s);
 stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum,
                           const double* Kt = nullptr);
+stdg_status visc_pc_apply32(stdg_solver* s, double nu, const float* r, float* z, const double* Kt);
+
+// Binary32 vector kernels of the inner COCG solves (cocg32.cu).  Vectors are [tet][time column][N];
+// the multipliers M (Ng x Ng, binary64 on the device) are block diagonal with blocks of size 1 or 2,
+// so only M[a][a-1..a+1] is read.  mix holds an Ng x Ng matrix applied to every tet's time columns.
+struct Mix32 { float v[kMaxNg * kMaxNg]; };
+void c32_mix_to32(cudaStream_t st, int ne, int N, int Ng, const Mix32& M, const double* in, float* out);
+void c32_mix_acc64(cudaStream_t st, int ne, int N, int Ng, const Mix32& M, const float* y, double* x);
+void c32_cross(cudaStream_t st, int ne, int N, int Ng, const float* u, const float* v, double* part);
+void c32_update(cudaStream_t st, int ne, int N, int Ng, const double* M, float* y, float* r, const float* p,
+                const float* q, const Mix32& W, double* part, int want);
+void c32_dir(cudaStream_t st, int ne, int N, int Ng, const double* M, const float* z, float* p);
 bool time_blockdiag(const double* K, int Ng, double* W, double* Winv, double* R, int* pair);
 void prof_fold(stdg_solver* s);
 }  // namespace stdg

@@ -124,11 +124,11 @@ struct SmallK { float v[kMaxNg * kMaxNg]; };
 // FP64-pipe-bound on sm_103a); the result is a fixed linear map of r, as preconditioning requires.
 // K may be any Ng x Ng matrix whose symmetric part is positive semidefinite (the time matrix, or
 // its real block-diagonal form).
-template <int NC>
+template <int NC, typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const float* __restrict__ U,
                                                  const float* __restrict__ lam, const double* __restrict__ detJ,
-                                                 SmallK K, float c, const double* __restrict__ r,
-                                                 double* __restrict__ z, int accum) {
+                                                 SmallK K, float c, const TI* __restrict__ r,
+                                                 TO* __restrict__ z, int accum) {
   extern __shared__ float vs[];
   const int N = NC ? NC : Nrt;
   const int Nst = N * Ng, NU = N * (N + 1);
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
       for (int a = 0; a < kMaxNg; ++a)
         if (a < Ng) {
           const size_t o = (size_t)i * Nst + a * N + k;
-          z[o] = accum ? z[o] + (double)zz[a] : (double)zz[a];
+          z[o] = accum ? z[o] + (TO)zz[a] : (TO)zz[a];
         }
     }
   }
@@ -222,10 +222,10 @@ __global__ void __launch_bounds__(256) k_visc_fd(int ne, int Nrt, int Ng, const 
 // The same with N and Ng at compile time (the solve's N, the time degree's Ng): the small solve is
 // unrolled with constant indices and U is staged by a plain contiguous copy (the tets of a pass are
 // consecutive), read by rows from its unpadded layout.
-template <int N, int NG>
+template <int N, int NG, typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_visc_fd_t(int ne, const float* __restrict__ U, const float* __restrict__ lam,
                                                    const double* __restrict__ detJ, SmallK K, float c,
-                                                   const double* __restrict__ r, double* __restrict__ z, int accum) {
+                                                   const TI* __restrict__ r, TO* __restrict__ z, int accum) {
   constexpr int Nst = N * NG, NN = N * N, TB = 256 / N;
   __shared__ __align__(16) float vs[TB * Nst];
   __shared__ __align__(16) float us[TB * NN];      // read as float4 when NN % 4 == 0
@@ -308,21 +308,21 @@ __global__ void __launch_bounds__(256) k_visc_fd_t(int ne, const float* __restri
 #pragma unroll
       for (int a = 0; a < NG; ++a) {
         const size_t o = (size_t)i * Nst + a * N + k;
-        z[o] = accum ? z[o] + (double)zz[a] : (double)zz[a];
+        z[o] = accum ? z[o] + (TO)zz[a] : (TO)zz[a];
       }
     }
   }
 }
 
-template <int N>
+template <int N, typename TI, typename TO>
 static void launch_fd_t(int Ng, int blocks, cudaStream_t st, int ne, const float* U, const float* lam,
-                        const double* detJ, const SmallK& K, float c, const double* r, double* z, int accum) {
+                        const double* detJ, const SmallK& K, float c, const TI* r, TO* z, int accum) {
   switch (Ng) {
-    case 1: k_visc_fd_t<N, 1><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 2: k_visc_fd_t<N, 2><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 3: k_visc_fd_t<N, 3><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 4: k_visc_fd_t<N, 4><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    default: k_visc_fd_t<N, 5><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 1: k_visc_fd_t<N, 1, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 2: k_visc_fd_t<N, 2, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 3: k_visc_fd_t<N, 3, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 4: k_visc_fd_t<N, 4, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    default: k_visc_fd_t<N, 5, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
   }
 }
 
@@ -486,7 +486,8 @@ stdg_status visc_pc_ensure(stdg_solver* s) {
 
 // z = D^-1 r (accum: z += D^-1 r) for the viscous operator with viscosity nu; with Kt, for the
 // operator whose time matrix is Kt instead of K (the block-diagonal form of the decoupled solve).
-stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum, const double* Kt) {
+template <typename TI, typename TO>
+static stdg_status visc_pc_launch(stdg_solver* s, double nu, const TI* r, TO* z, int accum, const double* Kt) {
   SmallK K{};
   for (int c = 0; c < s->Ng * s->Ng; ++c) K.v[c] = (float)(Kt ? Kt[c] : s->K[c]);
   const int N = s->N, TB = 256 / N;
@@ -498,10 +499,22 @@ stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z,
     case 20: launch_fd_t<20>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
     case 35: launch_fd_t<35>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
     case 10: launch_fd_t<10>(s->Ng, blocks, s->stream, (int)s->ne, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
-    default: k_visc_fd<0><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z, accum); break;
+    default:
+      k_visc_fd<0, TI, TO><<<blocks, 256, smem, s->stream>>>((int)s->ne, N, s->Ng, s->vpcU, s->vpcLam, s->dm.detJ, K, c, r, z,
+                                                              accum);
+      break;
   }
   STDG_LAUNCH_CHECK();
   return STDG_OK;
+}
+
+stdg_status visc_pc_apply(stdg_solver* s, double nu, const double* r, double* z, int accum, const double* Kt) {
+  return visc_pc_launch(s, nu, r, z, accum, Kt);
+}
+
+// binary32 vectors in and out (the inner solves of the mixed-precision viscous refinement)
+stdg_status visc_pc_apply32(stdg_solver* s, double nu, const float* r, float* z, const double* Kt) {
+  return visc_pc_launch(s, nu, r, z, 0, Kt);
 }
 
 }  // namespace stdg
