@@ -577,21 +577,27 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int Nrt, int Ng, con
 }
 // The update and the preconditioner of one binary32 CG iteration in one pass: x += alpha_a p,
 // r -= alpha_a q (alpha from the device), then z = Binv r from the updated rows kept in shared
-// memory (thread per (tet, row), all columns), and partials of r.z per column.
-template <int NC>
-__global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ng, const double* __restrict__ alpha,
+// memory (thread per (tet, row), all columns), and partials of r.z per column.  With N and Ng at
+// compile time (NC, NGC != 0) a thread's N column loads of Binv are all issued before its first
+// multiply-add, so each warp keeps N loads in flight.
+template <int NC, int NGC>
+__global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ngrt, const double* __restrict__ alpha,
                                                      float* __restrict__ x, float* __restrict__ r,
                                                      const float* __restrict__ p, const float* __restrict__ q,
                                                      const float* __restrict__ Binv, float* __restrict__ z,
                                                      double* part) {
+  constexpr int NGM = NGC ? NGC : kMaxNg;
   extern __shared__ float rs[];
   __shared__ float s_al[kMaxNg];
+  const int Ng = NGC ? NGC : Ngrt;
   if (threadIdx.x < Ng) s_al[threadIdx.x] = (float)alpha[threadIdx.x];
   const int N = NC ? NC : Nrt;
   const int Nst = N * Ng;
   const int TB = blockDim.x / N;
   const size_t NN = (size_t)N * N;
-  float acc[kMaxNg] = {0, 0, 0, 0, 0};
+  float acc[NGM];
+#pragma unroll
+  for (int a = 0; a < NGM; ++a) acc[a] = 0.0f;
   const int tl = threadIdx.x / N, k = threadIdx.x - tl * N;
   for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
     __syncthreads();
@@ -609,17 +615,30 @@ __global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ng, c
     if (tl < TB && i < ne) {
       const float* B = Binv + (size_t)i * NN + k;
       const float* rr = rs + tl * Nst;
-      float sa[kMaxNg] = {0, 0, 0, 0, 0};
-#pragma unroll 4
-      for (int l2 = 0; l2 < N; ++l2) {
-        const float b = B[(size_t)l2 * N];
+      float sa[NGM];
 #pragma unroll
-        for (int a = 0; a < kMaxNg; ++a)
-          if (a < Ng) sa[a] = fmaf(b, rr[a * N + l2], sa[a]);
+      for (int a = 0; a < NGM; ++a) sa[a] = 0.0f;
+      if constexpr (NC > 0) {
+        float bv[NC];
+#pragma unroll
+        for (int l2 = 0; l2 < NC; ++l2) bv[l2] = __ldg(B + (size_t)l2 * NC);
+#pragma unroll
+        for (int l2 = 0; l2 < NC; ++l2)
+#pragma unroll
+          for (int a = 0; a < NGM; ++a)
+            if (NGC || a < Ng) sa[a] = fmaf(bv[l2], rr[a * NC + l2], sa[a]);
+      } else {
+#pragma unroll 4
+        for (int l2 = 0; l2 < N; ++l2) {
+          const float b = B[(size_t)l2 * N];
+#pragma unroll
+          for (int a = 0; a < NGM; ++a)
+            if (a < Ng) sa[a] = fmaf(b, rr[a * N + l2], sa[a]);
+        }
       }
 #pragma unroll
-      for (int a = 0; a < kMaxNg; ++a)
-        if (a < Ng) {
+      for (int a = 0; a < NGM; ++a)
+        if (NGC || a < Ng) {
           z[(size_t)i * Nst + a * N + k] = sa[a];
           acc[a] = fmaf(sa[a], rr[a * N + k], acc[a]);
         }
@@ -627,7 +646,8 @@ __global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ng, c
   }
   __syncthreads();
   double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int a = 0; a < kMaxNg; ++a) d[a] = acc[a];
+#pragma unroll
+  for (int a = 0; a < NGM; ++a) d[a] = acc[a];
   lp_block_store(d, Ng, part, Ng);
 }
 
@@ -635,12 +655,12 @@ void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alp
                        const float* q, const float* Binv, float* z, double* part) {
   const int TB = 256 / N;
   const size_t smem = (size_t)TB * N * Ng * sizeof(float);
-  switch (N) {
-    case 20: k_lp_update_bj<20><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
-    case 35: k_lp_update_bj<35><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
-    case 10: k_lp_update_bj<10><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
-    default: k_lp_update_bj<0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part); break;
-  }
+  if (N == 35 && Ng == 5) k_lp_update_bj<35, 5><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
+  else if (N == 20 && Ng == 2) k_lp_update_bj<20, 2><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
+  else if (N == 35) k_lp_update_bj<35, 0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
+  else if (N == 20) k_lp_update_bj<20, 0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
+  else if (N == 10) k_lp_update_bj<10, 0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
+  else k_lp_update_bj<0, 0><<<kLpBlocks, 256, smem, st>>>(ne, N, Ng, alpha, x, r, p, q, Binv, z, part);
 }
 
 // out = float(coef * Sum_b M[a][b] in[b])   (time mixing + conversion)

@@ -500,6 +500,31 @@ def test_step_matches_oracle_at_benchmarked_degrees(p, pt, npic, precision, meth
     assert max(st["press_residual"]) <= 1e-11
 
 
+@pytest.mark.parametrize("p,pt,npic", [(3, 1, 3), (4, 4, 2)])
+@pytest.mark.parametrize("inner64", [False, True])
+def test_mixed_viscous_inner_solves_match_oracle(p, pt, npic, inner64, monkeypatch):
+    """The mixed-precision viscous solves (binary64 refinement around inner COCG solves of the
+    time-decoupled systems of Eq. A1_mod) with binary32 inner vectors (default) and with binary64
+    inner vectors (STDG_VISC_INNER64=1): the step matches the oracle's to 1e-10 either way, and the
+    viscous solves reach their binary64 tolerance."""
+    import paper_1601_07384_gb300 as g
+    if inner64:
+        monkeypatch.setenv("STDG_VISC_INNER64", "1")
+    nu, dt = 0.1, 0.01
+    d, so1, Uo = _oracle_beltrami_step(p, pt, npic, nu, dt)
+    prm = BeltramiParams(nu=nu)
+    v, t = kuhn_mesh(2, seed=0)
+    gs = g.Solver(g.Mesh(v, t), g.Reference(p, pt), dt, precision="mixed_f32")
+    gs.set_initial(g.beltrami(prm.a, prm.d, prm.nu))
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    st = gs.step(nu, npic, method="kron_mg", tol=1e-13)
+    P, V, _ = gs.get_state()
+    ep = rel(P.cpu().numpy(), so1.P.ravel())
+    ev = rel(_moments(gs, d, V), Uo)
+    print(f"p={p} pt={pt} inner64={inner64}: pressure {ep:.2e} velocity {ev:.2e} visc iters {st['visc_iters']}")
+    assert ep <= STEP_TOL and ev <= STEP_TOL
+
+
 @pytest.mark.parametrize("tol,bound", [(1e-13, STEP_TOL), (1e-12, 1e-8)])
 def test_tiny_configuration_five_steps(tol, bound):
     """The tiny configuration end to end: 3^3 hexahedra x 6 = 162 jittered tets, p = 1, p_t = 0,
