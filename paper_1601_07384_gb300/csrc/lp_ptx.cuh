@@ -93,4 +93,22 @@ __device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
   e = (a - (s - bb)) + (b - bb);
 }
 
+// packed binary32 subtraction (sub.rn.f32x2, sm_100 and later)
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// error-free difference on both halves of two float2 values: s + e = a - b exactly
+// (the sum above with b negated, the negation folded into the operations)
+__device__ __forceinline__ void df_two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = f2_sub(a, b);
+  const float2 bb = f2_sub(s, a);                 // -b as far as s carries it
+  e = f2_sub(f2_sub(a, f2_sub(s, bb)), __fadd2_rn(b, bb));
+}
+
 }  // namespace stdg

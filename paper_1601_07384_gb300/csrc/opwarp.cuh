@@ -45,53 +45,72 @@ __device__ __forceinline__ void load_row4(const __nv_bfloat16* B, int idx, float
 __device__ __forceinline__ float load_one(const float* B, int idx) { return B[idx]; }
 __device__ __forceinline__ float load_one(const __nv_bfloat16* B, int idx) { return __bfloat162float(B[idx]); }
 
-// binary64-accurate multiply-add from binary32 pairs: (h, l) += (bh + bl)(zh + zl); the bl zl term
-// (relative size 2^-48) is left out
-__device__ __forceinline__ void df_fma(float& h, float& l, float bh, float bl, float zh, float zl) {
-  const float p = bh * zh;
-  float e = fmaf(bh, zh, -p);
-  e = fmaf(bh, zl, e);
-  e = fmaf(bl, zh, e);
-  float s, t;
-  df_two_sum(h, p, s, t);
-  h = s;
-  l += t + e;
-}
-
 __host__ __device__ constexpr int warp_np_c(int N) { return N % 8 == 4 ? N : warp_np_c(N + 1); }
 __host__ __device__ constexpr int warp_nr_c(int N) { return (N + 3) / 4 * 4; }
 
-// four entries of a block row (stride 1: one vector load) or column (stride NP: four loads) times
-// the matching z entries, accumulated into one chain per time column
-template <bool DF, int NG, typename TB>
-__device__ __forceinline__ void warp_chunk(const TB* B, int stride, uint32_t plane, const float* z, int NR,
-                                           int zplane, float (&h)[NG], float (&lo)[NG]) {
-  float bh[4], bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+// Binary64-accurate multiply-add from binary32 pairs, (h, l) += (bh + bl)(zh + zl) with the bl zl
+// term (relative size 2^-48) left out: the product bh zh split exactly by a fused multiply-add, its
+// high part added to h by an error-free sum.  Two independent accumulators at once (the halves of
+// the float2 values), in packed binary32 operations (f32x2, sm_100 and later).  nbh = -bh, formed
+// once per chunk: pn = nbh zh is the rounded product negated exactly, so no negation per product.
+__device__ __forceinline__ void df_fma2(float2& h, float2& l, float2 bh, float2 nbh, float2 bl, float2 zh, float2 zl) {
+  const float2 pn = __fmul2_rn(nbh, zh);
+  float2 e = __ffma2_rn(bh, zh, pn);              // bh zh - p, exact
+  e = __ffma2_rn(bh, zl, e);
+  e = __ffma2_rn(bl, zh, e);
+  float2 s, t;
+  df_two_diff2(h, pn, s, t);                      // h + p = h - pn, error-free
+  h = s;
+  l = __fadd2_rn(l, __fadd2_rn(t, e));
+}
+
+// pair policy: four entries of a block row (stride 1: vector loads of the hi and lo planes) or
+// column (stride NP) times the matching z entries; entries (0, 1) and (2, 3) through the two halves
+// of (h, l), one accumulator pair per time column
+template <int NG, typename TB>
+__device__ __forceinline__ void warp_chunk_df2(const TB* B, int stride, uint32_t plane, const float* z, int NR,
+                                               int zplane, float2 (&h)[NG], float2 (&l)[NG]) {
+  float bh[4], bl[4];
   if (stride == 1) {
     load_row4(B, 0, bh);
-    if constexpr (DF) load_row4(B + plane, 0, bl);
+    load_row4(B + plane, 0, bl);
   } else {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       bh[u] = load_one(B, u * stride);
-      if constexpr (DF) bl[u] = load_one(B + plane, u * stride);
+      bl[u] = load_one(B + plane, u * stride);
     }
   }
+  const float2 bh01 = make_float2(bh[0], bh[1]), bh23 = make_float2(bh[2], bh[3]);
+  const float2 nb01 = make_float2(-bh[0], -bh[1]), nb23 = make_float2(-bh[2], -bh[3]);
+  const float2 bl01 = make_float2(bl[0], bl[1]), bl23 = make_float2(bl[2], bl[3]);
 #pragma unroll
   for (int q = 0; q < NG; ++q) {
     const float4 zh = *reinterpret_cast<const float4*>(z + q * NR);
-    if constexpr (DF) {
-      const float4 zl = *reinterpret_cast<const float4*>(z + zplane + q * NR);
-      df_fma(h[q], lo[q], bh[0], bl[0], zh.x, zl.x);
-      df_fma(h[q], lo[q], bh[1], bl[1], zh.y, zl.y);
-      df_fma(h[q], lo[q], bh[2], bl[2], zh.z, zl.z);
-      df_fma(h[q], lo[q], bh[3], bl[3], zh.w, zl.w);
-    } else {                                      // two independent chains per chunk (h, lo)
-      h[q] = fmaf(bh[0], zh.x, h[q]);
-      lo[q] = fmaf(bh[1], zh.y, lo[q]);
-      h[q] = fmaf(bh[2], zh.z, h[q]);
-      lo[q] = fmaf(bh[3], zh.w, lo[q]);
-    }
+    const float4 zl = *reinterpret_cast<const float4*>(z + zplane + q * NR);
+    df_fma2(h[q], l[q], bh01, nb01, bl01, make_float2(zh.x, zh.y), make_float2(zl.x, zl.y));
+    df_fma2(h[q], l[q], bh23, nb23, bl23, make_float2(zh.z, zh.w), make_float2(zl.z, zl.w));
+  }
+}
+
+// binary32 policies: the same four-entry chunk with packed multiply-adds, entries (0, 1) and (2, 3)
+// in the two halves of one float2 accumulator per time column (fma.rn.f32x2: half the issue slots of
+// four scalar multiply-adds, the same binary32 rounding)
+template <int NG, typename TB>
+__device__ __forceinline__ void warp_chunk2(const TB* B, int stride, const float* z, int NR, float2 (&acc)[NG]) {
+  float b[4];
+  if (stride == 1) {
+    load_row4(B, 0, b);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = load_one(B, u * stride);
+  }
+  const float2 b01 = make_float2(b[0], b[1]), b23 = make_float2(b[2], b[3]);
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    const float4 zv = *reinterpret_cast<const float4*>(z + q * NR);
+    acc[q] = __ffma2_rn(b01, make_float2(zv.x, zv.y), acc[q]);
+    acc[q] = __ffma2_rn(b23, make_float2(zv.z, zv.w), acc[q]);
   }
 }
 
@@ -288,9 +307,13 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
     const int nmain = N < 32 ? N : 32;
     if (lane < nmain) {
       const int k = lane;
-      float h0[NG], l0[NG], h1[NG], l1[NG];       // two accumulator chains per time column
+      float2 dh[NG], dl[NG];                      // pair policy: packed (hi, lo) accumulators per column
+      float2 c0[NG], c1[NG];                      // binary32 policies: two packed accumulators per column
 #pragma unroll
-      for (int q = 0; q < NG; ++q) { h0[q] = h1[q] = 0.0f; l0[q] = l1[q] = 0.0f; }
+      for (int q = 0; q < NG; ++q) {
+        dh[q] = dl[q] = make_float2(0.0f, 0.0f);
+        c0[q] = c1[q] = make_float2(0.0f, 0.0f);
+      }
       // pair policy at N > 20 (about 200 instructions per chunk): the block and chunk loops stay rolled,
       // as fully unrolled code outgrows the instruction cache
       auto block_main = [&](int sl) {
@@ -301,15 +324,25 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
           const TB* Br = B + k * NP;
 #pragma unroll (kRoll ? 1 : 8)
           for (int l = 0; l < NR; l += 8) {
-            warp_chunk<kDF, NG>(Br + l, 1, a.plane_elems, z + l, NR, zplane, h0, l0);
-            if (l + 4 < NR) warp_chunk<kDF, NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
+            if constexpr (kDF) {
+              warp_chunk_df2<NG>(Br + l, 1, a.plane_elems, z + l, NR, zplane, dh, dl);
+              if (l + 4 < NR) warp_chunk_df2<NG>(Br + l + 4, 1, a.plane_elems, z + l + 4, NR, zplane, dh, dl);
+            } else {
+              warp_chunk2<NG>(Br + l, 1, z + l, NR, c0);
+              if (l + 4 < NR) warp_chunk2<NG>(Br + l + 4, 1, z + l + 4, NR, c1);
+            }
           }
         } else {                                  // column k: A_rl = A_lr^T, one word per lane
           const TB* Bc = B + k;
 #pragma unroll (kRoll ? 1 : 8)
           for (int l = 0; l < NR; l += 8) {
-            warp_chunk<kDF, NG>(Bc + l * NP, NP, a.plane_elems, z + l, NR, zplane, h0, l0);
-            if (l + 4 < NR) warp_chunk<kDF, NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, NR, zplane, h1, l1);
+            if constexpr (kDF) {
+              warp_chunk_df2<NG>(Bc + l * NP, NP, a.plane_elems, z + l, NR, zplane, dh, dl);
+              if (l + 4 < NR) warp_chunk_df2<NG>(Bc + (l + 4) * NP, NP, a.plane_elems, z + l + 4, NR, zplane, dh, dl);
+            } else {
+              warp_chunk2<NG>(Bc + l * NP, NP, z + l, NR, c0);
+              if (l + 4 < NR) warp_chunk2<NG>(Bc + (l + 4) * NP, NP, z + l + 4, NR, c1);
+            }
           }
         }
       };
@@ -324,10 +357,10 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
       for (int q = 0; q < NG; ++q) {
         if constexpr (kDF) {
           float s, t;
-          df_two_sum(h0[q], h1[q], s, t);
-          v[q] = (double)s + (double)(t + (l0[q] + l1[q]));   // the error terms are ~2^-24 of s
+          df_two_sum(dh[q].x, dh[q].y, s, t);
+          v[q] = (double)s + (double)(t + (dl[q].x + dl[q].y));   // the error terms are ~2^-24 of s
         } else {
-          v[q] = (h0[q] + l0[q]) + (h1[q] + l1[q]);
+          v[q] = (c0[q].x + c0[q].y) + (c1[q].x + c1[q].y);
         }
       }
       finish(k, v);
@@ -335,9 +368,9 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
     if (N > 32) {                                 // rows 32 .. N-1: 8 lanes per row, chunks split
       const int g = lane >> 3, c = lane & 7, r = 32 + g;
       const int nch = NR / 4;
-      float eh[NG], el[NG];
+      float2 eh[NG], el[NG], ec[NG];
 #pragma unroll
-      for (int q = 0; q < NG; ++q) { eh[q] = 0.0f; el[q] = 0.0f; }
+      for (int q = 0; q < NG; ++q) eh[q] = el[q] = ec[q] = make_float2(0.0f, 0.0f);
       if (r < N) {
 #pragma unroll (kRoll ? 1 : 5)
         for (int sl = 0; sl < 5; ++sl) {
@@ -347,16 +380,27 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
           const bool tr = (trm >> sl) & 1;
           for (int ch = c; ch < nch; ch += 8) {
             const int l = 4 * ch;
-            if (!tr) warp_chunk<kDF, NG>(B + r * NP + l, 1, a.plane_elems, z + l, NR, zplane, eh, el);
-            else warp_chunk<kDF, NG>(B + l * NP + r, NP, a.plane_elems, z + l, NR, zplane, eh, el);
+            if constexpr (kDF) {
+              if (!tr) warp_chunk_df2<NG>(B + r * NP + l, 1, a.plane_elems, z + l, NR, zplane, eh, el);
+              else warp_chunk_df2<NG>(B + l * NP + r, NP, a.plane_elems, z + l, NR, zplane, eh, el);
+            } else {
+              if (!tr) warp_chunk2<NG>(B + r * NP + l, 1, z + l, NR, ec);
+              else warp_chunk2<NG>(B + l * NP + r, NP, z + l, NR, ec);
+            }
           }
         }
       }
       Real v[NG];
 #pragma unroll
       for (int q = 0; q < NG; ++q) {
-        float h = eh[q], e = el[q];
-        if constexpr (!kDF) { h += e; e = 0.0f; }
+        float h, e;
+        if constexpr (kDF) {
+          df_two_sum(eh[q].x, eh[q].y, h, e);
+          e += el[q].x + el[q].y;
+        } else {
+          h = ec[q].x + ec[q].y;
+          e = 0.0f;
+        }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {         // within the 8-lane group
           const float oh = __shfl_xor_sync(0xffffffffu, h, o), oe = __shfl_xor_sync(0xffffffffu, e, o);
