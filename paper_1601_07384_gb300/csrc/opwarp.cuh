@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "lp_ptx.cuh"
 #include "solver.h"
 
@@ -22,6 +24,7 @@ struct WarpArgs {
   uint32_t blk_bytes;           // one padded block (all planes)
   uint32_t plane_elems;         // NR * NP
   uint32_t xraw_off, stage_bytes, z_off, bar_off, warp_bytes;
+  uint32_t red_off;             // CTA kernels: partial sums [warp][NR][Ng] of the output rows
   double scale, pin_diag;
   double Tacc[kMaxNg * kMaxNg];
   // viscous operator (Eq. A1_mod): + mass_coef |J_i| (K (x) I) x_i, exact in the input precision
@@ -455,6 +458,311 @@ __global__ void __launch_bounds__(128, 1) k_apply_warp(WarpArgs a, const typenam
   }
 }
 
+// The same operator with WPC warps sharing each staged tet, for the pair policy at N = 35, where the
+// warp kernel fits only three warps per SM.  One CTA per stride of tets (persistent grid); S stages
+// (two where two CTAs still fit: the next tet's copies land while this one computes).  Thread 0 stages the
+// five blocks by 1-D TMA bulk copies, all threads stage the x rows by cp.async, on the stage's
+// mbarrier.  The (block, four-column chunk) products of a tet are dealt out round robin: warp w
+// takes products w, w + WPC, ..., one lane per output row 0..31, and for rows 32..N-1 one group of
+// 8 lanes per row over the same products.  Each warp leaves its partial sums in shared memory;
+// one thread per output row adds the WPC partials and finishes the row (time mixing, scale, mass
+// term, pin, store, x.y partials).  Per tet: wait, prepare (pin; pair policy: x split into hi/lo
+// planes), barrier, products, barrier, rows, barrier, refill the stage.  Every wait is bounded.
+// component k (0..3) of an int4 by selects (no local-memory array for a runtime k)
+__device__ __forceinline__ int pick4(const int4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+// the tet whose x slot sl (0: tet i itself, 1..4: the neighbour across face sl - 1) holds, or -1
+__device__ __forceinline__ int slot_tet(int i, int sl, const int4& gf, const int4& gn) {
+  return sl == 0 ? i : (pick4(gf, sl - 1) >= 0 ? pick4(gn, sl - 1) : -1);
+}
+
+template <typename W, int NG, int NC, int WPC>
+__global__ void __launch_bounds__(32 * WPC) k_apply_cta(WarpArgs a, const typename W::XIn* __restrict__ x,
+                                                       typename W::YOut* __restrict__ y) {
+  using TB = typename W::TB;
+  using XIn = typename W::XIn;
+  using Real = typename W::Real;
+  constexpr bool kDF = W::kPlanes == 2;
+  using Part = typename std::conditional<kDF, float2, float>::type;
+  constexpr int NT = 32 * WPC;
+  extern __shared__ __align__(128) unsigned char csm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* zs = reinterpret_cast<float*>(csm + a.z_off);
+  Part* red = reinterpret_cast<Part*>(csm + a.red_off);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(csm + a.bar_off);
+  const int N = NC ? NC : a.N, NR = NC ? warp_nr_c(NC) : a.NR, NP = NC ? warp_np_c(NC) : a.NP;
+  const int Nst = NC ? NC * NG : a.Nst, S = a.S;
+  const int nch = NR / 4, npair = 5 * nch;
+  const Real scale = (Real)a.scale;
+  const bool has_mass = a.mass_coef != 0.0, kron = a.kron != 0, pinned = a.pinned != 0;
+  const int zplane = 5 * NG * NR;
+  __shared__ Real sT[NG * NG], sK[NG * NG];       // time matrices in the arithmetic type, converted once
+  if (tid < NG * NG) { sT[tid] = (Real)a.Tacc[tid]; sK[tid] = (Real)a.Kmass[tid]; }
+  if constexpr (kDF) {
+    for (int e = tid; e < 2 * zplane; e += NT) zs[e] = 0.0f;             // padding entries stay 0
+  } else {
+    for (int st = 0; st < S; ++st) {
+      float* xz = reinterpret_cast<float*>(csm + (size_t)st * a.stage_bytes + a.xraw_off);
+      for (int e = tid; e < zplane; e += NT) xz[e] = 0.0f;
+    }
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1 + NT);   // thread 0's expect_tx + NT cp.async arrivals
+    fence_async_smem();
+  }
+  __syncthreads();
+
+  auto issue = [&](int i, int st) {
+    unsigned char* sb = csm + (size_t)st * a.stage_bytes;
+    XIn* xr = reinterpret_cast<XIn*>(sb + a.xraw_off);
+    const int4 gf = a.gface[i], gn = a.gnbr[i];
+    const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
+    if (tid == 0) {
+      uint32_t bytes = a.blk_bytes;
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fj[f] >= 0) bytes += a.blk_bytes;
+      fence_async_smem();                         // earlier generic reads of this stage before the copies
+      mbar_expect_tx(&bar[st], bytes);
+      tma_load_1d(sb, static_cast<const unsigned char*>(a.Bd) + (size_t)i * a.blk_bytes, a.blk_bytes, &bar[st]);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fj[f] >= 0)
+          tma_load_1d(sb + (size_t)(f + 1) * a.blk_bytes,
+                      static_cast<const unsigned char*>(a.Ao) + (size_t)(fj[f] >> 1) * a.blk_bytes, a.blk_bytes,
+                      &bar[st]);
+    }
+    if constexpr (kDF) {
+      for (int idx = tid; idx < 5 * Nst; idx += NT) {
+        const int sl = idx / Nst, o = idx - sl * Nst;
+        const int nb = slot_tet(i, sl, gf, gn);
+        if (nb >= 0) cp_async<sizeof(XIn)>(xr + idx, x + (size_t)nb * Nst + o);
+      }
+    } else {
+      for (int idx = tid; idx < 5 * NG * N; idx += NT) {
+        const int rw = idx / N, l = idx - rw * N, sl = rw / NG;   // row rw = (slot, time column)
+        const int nb = slot_tet(i, sl, gf, gn);
+        if (nb >= 0) cp_async<sizeof(XIn)>(xr + rw * NR + l, x + (size_t)nb * Nst + (rw - sl * NG) * N + l);
+      }
+    }
+    cp_async_mbar_arrive_noinc(&bar[st]);
+  };
+
+  const int grid = gridDim.x;
+  float dacc[NG];                                 // x_i . y_i of this thread's rows (dotpart)
+#pragma unroll
+  for (int q = 0; q < NG; ++q) dacc[q] = 0.0f;
+  int i = blockIdx.x;
+  for (int k = 0; k < S; ++k)
+    if (i + k * grid < a.ne) issue(i + k * grid, k);
+  bool abort = false;
+  int it = 0;
+  for (; i < a.ne; i += grid, ++it) {
+    const int st = S == 2 ? (it & 1) : 0;
+    {
+      long spins = 0;
+      const uint32_t par = (uint32_t)((it / S) & 1);
+      while (!mbar_wait_hint(&bar[st], par))
+        if (++spins > kWarpSpin) { abort = true; break; }
+    }
+    if (__syncthreads_or(abort)) { abort = true; break; }
+    if (kDF && tid == 0 && i + S * grid < a.ne) {   // the blocks after the next staged tet: towards L2
+      const int ip = i + S * grid;
+      const int4 gp = a.gface[ip];
+      const int fp[4] = {gp.x, gp.y, gp.z, gp.w};
+      bulk_prefetch_l2(static_cast<const unsigned char*>(a.Bd) + (size_t)ip * a.blk_bytes, a.blk_bytes);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (fp[f] >= 0)
+          bulk_prefetch_l2(static_cast<const unsigned char*>(a.Ao) + (size_t)(fp[f] >> 1) * a.blk_bytes, a.blk_bytes);
+    }
+    unsigned char* sb = csm + (size_t)st * a.stage_bytes;
+    XIn* xr = reinterpret_cast<XIn*>(sb + a.xraw_off);
+    const int4 gf = a.gface[i], gn = a.gnbr[i];
+    const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
+    // pinned entries (constant mode of tet 0, every time column) read as 0
+    if constexpr (kDF) {
+      for (int idx = tid; idx < 5 * NG * N; idx += NT) {
+        const int rw = idx / N, l = idx - rw * N, sl = rw / NG;
+        const int nb = slot_tet(i, sl, gf, gn);
+        if (nb < 0) continue;
+        XIn v = xr[sl * Nst + (rw - sl * NG) * N + l];
+        if (pinned && nb == 0 && l == 0) v = (XIn)0;
+        const float2 hl = df_split(v);
+        zs[rw * NR + l] = hl.x;
+        zs[zplane + rw * NR + l] = hl.y;
+      }
+    } else if (pinned && tid < 5 * NG) {
+      const int nb = slot_tet(i, tid / NG, gf, gn);
+      if (nb == 0) xr[tid * NR] = (XIn)0;
+    }
+    __syncthreads();
+    const float* zb = kDF ? zs : reinterpret_cast<const float*>(xr);   // z rows [slot][q][NR]
+    const TB* blk = reinterpret_cast<const TB*>(sb);
+    const int blk_elems = (int)(a.blk_bytes / sizeof(TB));
+    int pres = 1, trm = 0;                        // per slot: block present / read transposed
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      pres |= (fj[f] >= 0 ? 1 : 0) << (f + 1);
+      trm |= (fj[f] >= 0 && (fj[f] & 1) ? 1 : 0) << (f + 1);
+    }
+    // rows 0..31: lane k, this warp's share of the products
+    if (lane < N) {
+      const int k = lane;
+      float2 dh[NG], dl[NG], c0[NG];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) dh[q] = dl[q] = c0[q] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+      for (int pr = warp; pr < npair; pr += WPC) {
+        const int sl = pr / nch, l = 4 * (pr - sl * nch);
+        if (!((pres >> sl) & 1)) continue;
+        const TB* B = blk + sl * blk_elems;
+        const float* z = zb + sl * NG * NR + l;
+        const bool tr = (trm >> sl) & 1;
+        if constexpr (kDF) {
+          if (!tr) warp_chunk_df2<NG>(B + k * NP + l, 1, a.plane_elems, z, NR, zplane, dh, dl);
+          else warp_chunk_df2<NG>(B + l * NP + k, NP, a.plane_elems, z, NR, zplane, dh, dl);
+        } else {
+          if (!tr) warp_chunk2<NG>(B + k * NP + l, 1, z, NR, c0);
+          else warp_chunk2<NG>(B + l * NP + k, NP, z, NR, c0);
+        }
+      }
+      Part* rp = red + ((size_t)warp * NR + k) * NG;
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        if constexpr (kDF) {
+          float s, t;
+          df_two_sum(dh[q].x, dh[q].y, s, t);
+          rp[q] = make_float2(s, t + (dl[q].x + dl[q].y));
+        } else {
+          rp[q] = c0[q].x + c0[q].y;
+        }
+      }
+    }
+    if (N > 32) {                                 // rows 32 .. N-1: 8 lanes per row over the warp's products
+      const int g = lane >> 3, c = lane & 7, r = 32 + g;
+      float2 eh[NG], el[NG], ec[NG];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) eh[q] = el[q] = ec[q] = make_float2(0.0f, 0.0f);
+      if (r < N) {
+#pragma unroll 1
+        for (int pr = warp + WPC * c; pr < npair; pr += 8 * WPC) {
+          const int sl = pr / nch, l = 4 * (pr - sl * nch);
+          if (!((pres >> sl) & 1)) continue;
+          const TB* B = blk + sl * blk_elems;
+          const float* z = zb + sl * NG * NR + l;
+          const bool tr = (trm >> sl) & 1;
+          if constexpr (kDF) {
+            if (!tr) warp_chunk_df2<NG>(B + r * NP + l, 1, a.plane_elems, z, NR, zplane, eh, el);
+            else warp_chunk_df2<NG>(B + l * NP + r, NP, a.plane_elems, z, NR, zplane, eh, el);
+          } else {
+            if (!tr) warp_chunk2<NG>(B + r * NP + l, 1, z, NR, ec);
+            else warp_chunk2<NG>(B + l * NP + r, NP, z, NR, ec);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        float h, e;
+        if constexpr (kDF) {
+          df_two_sum(eh[q].x, eh[q].y, h, e);
+          e += el[q].x + el[q].y;
+        } else {
+          h = ec[q].x + ec[q].y;
+          e = 0.0f;
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {         // within the 8-lane group
+          const float oh = __shfl_xor_sync(0xffffffffu, h, o), oe = __shfl_xor_sync(0xffffffffu, e, o);
+          if constexpr (kDF) {
+            float s, t;
+            df_two_sum(h, oh, s, t);
+            h = s;
+            e = e + oe + t;
+          } else {
+            h += oh;
+          }
+        }
+        if (c == 0 && r < N) {
+          if constexpr (kDF) red[((size_t)warp * NR + r) * NG + q] = make_float2(h, e);
+          else red[((size_t)warp * NR + r) * NG + q] = h;
+        }
+      }
+    }
+    __syncthreads();
+    // output rows: the WPC partials of each, then time mixing, scale, mass term, pin, store, x.y
+    for (int k = tid; k < N; k += NT) {
+      Real v[NG];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        if constexpr (kDF) {
+          float h = 0.0f, e = 0.0f;
+#pragma unroll
+          for (int w = 0; w < WPC; ++w) {
+            const float2 pw = red[((size_t)w * NR + k) * NG + q];
+            float s, t;
+            df_two_sum(h, pw.x, s, t);
+            h = s;
+            e += pw.y + t;
+          }
+          v[q] = (double)h + (double)e;
+        } else {
+          float h = 0.0f;
+#pragma unroll
+          for (int w = 0; w < WPC; ++w) h += red[((size_t)w * NR + k) * NG + q];
+          v[q] = h;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        Real o = v[q];
+        if (!kron) {
+          o = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) o += sT[q * NG + b] * v[b];
+        }
+        o *= scale;
+        if (has_mass) {                           // x_i as staged (binary64 for the pair policy)
+          Real m = 0;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) m += sK[q * NG + b] * (Real)(kDF ? xr[b * N + k] : xr[b * NR + k]);
+          o += (Real)(a.mass_coef * a.detJ[i]) * m;
+        }
+        if (pinned && i == 0 && k == 0) o = (Real)a.pin_diag * (Real)x[q * N];
+        y[(size_t)i * Nst + q * N + k] = (typename W::YOut)o;
+        if (a.dotpart) dacc[q] += (float)((Real)x[(size_t)i * Nst + q * N + k] * o);
+      }
+    }
+    __syncthreads();                              // stage st and the partials are free again
+    if (i + S * grid < a.ne) issue(i + S * grid, st);
+  }
+  if (a.dotpart) {                                // fixed order: lanes by shuffle, warps by index
+    __shared__ float wdot[WPC][kMaxNg];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      float v = dacc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wdot[warp][q] = v;
+    }
+    __syncthreads();                              // every thread of the block reaches this point
+    if (tid < NG) {
+      double t = 0.0;
+      for (int w = 0; w < WPC; ++w) t += (double)wdot[w][tid];
+      a.dotpart[(size_t)blockIdx.x * NG + tid] = t;
+    }
+  }
+  if (abort) {
+    if (tid == 0) atomicExch(a.err, 1);
+    // bounded wait for the copies in flight: the stages of iterations it .. it + S - 1 that were issued
+    for (int k = 0; k < S; ++k) {
+      if (i + k * grid >= a.ne) break;
+      const int st = S == 2 ? ((it + k) & 1) : 0;
+      long spins = 0;
+      while (!mbar_wait_hint(&bar[st], (uint32_t)(((it + k) / S) & 1)) && ++spins < kWarpSpin) {
+      }
+    }
+  }
+}
+
 // padded block copies: dst block b = planes x NR x NP, zero outside N x N
 template <typename TB, int PLANES>
 __global__ void k_to_padded(int64_t nblk, int N, int NR, int NP, const double* __restrict__ src, TB* __restrict__ dst,
@@ -528,8 +836,37 @@ static WarpArgs warp_layout(const stdg_solver* s, size_t tb, int planes, size_t 
   return a;
 }
 
+// CTA kernels: the warp layout's stages and z planes, then the partial sums, then S mbarriers
+// (warp_bytes: bytes per CTA)
+static WarpArgs cta_layout(const stdg_solver* s, size_t tb, int planes, size_t xin, int S, int wpc) {
+  WarpArgs a = warp_layout(s, tb, planes, xin, S);
+  a.red_off = a.bar_off;
+  a.bar_off = a16(a.red_off + (size_t)wpc * a.NR * s->Ng * (planes == 2 ? 8 : 4));
+  a.warp_bytes = a16(a.bar_off + (size_t)S * sizeof(uint64_t));
+  return a;
+}
+
+// warps per CTA of the CTA kernels (pair policy): one 72 KB stage each at N = 35, three CTAs per SM
+constexpr int kCtaWarps = 4;
+
+// The CTA kernels serve the pair policy at N > 20, where one tet's products are long enough to
+// share among warps (N = 35: 19.2 -> 11.7 ms per application at 384,000 tets, the warp kernel fitting
+// three warps per SM); for the binary32 policies and at N <= 20 the per-tet work is too short for
+// three CTA barriers and the serial row pass (measured 1.4-2x slower), so the warp kernels serve.
+template <typename W>
+static bool use_cta(const stdg_solver* s) {
+  return s->op_cta != 0 && W::kPlanes == 2 && s->N > 20;
+}
+
 template <typename W>
 static WarpArgs warp_args(const stdg_solver* s) {
+  if (use_cta<W>(s)) {
+    // two stages when two CTAs fit on an SM with them, else one
+    WarpArgs a = cta_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 2, kCtaWarps);
+    if ((size_t)a.warp_bytes * 2 > 226 * 1024)
+      a = cta_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 1, kCtaWarps);
+    return a;
+  }
   // two stages when ten warps fit on an SM with them, else one (more warps hide the latency)
   WarpArgs a = warp_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 2);
   if ((size_t)a.warp_bytes * 10 > 228 * 1024) a = warp_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 1);
@@ -542,9 +879,13 @@ static constexpr int warp_kind() { return W::kPlanes == 2 ? 2 : (sizeof(typename
 template <typename W>
 using WarpKernel = void (*)(WarpArgs, const typename W::XIn*, typename W::YOut*);
 
-// the instantiation for this N: compile-time N for p = 2, 3, 4, runtime N otherwise
+// the instantiation for this N: compile-time N for p = 2, 3, 4, runtime N otherwise (CTA kernels:
+// pair policy only, see use_cta)
 template <typename W, int NG>
-static WarpKernel<W> warp_kernel(int N) {
+static WarpKernel<W> warp_kernel(int N, bool cta) {
+  if constexpr (W::kPlanes == 2) {
+    if (cta) return N == 35 ? k_apply_cta<W, NG, 35, kCtaWarps> : k_apply_cta<W, NG, 0, kCtaWarps>;
+  }
   switch (N) {
     case 10: return k_apply_warp<W, NG, 10>;
     case 20: return k_apply_warp<W, NG, 20>;
@@ -558,12 +899,24 @@ static WarpKernel<W> warp_kernel(int N) {
 template <typename W, int NG>
 static cudaError_t warp_configure(stdg_solver* s) {
   const WarpArgs a = warp_args<W>(s);
-  const WarpKernel<W> kern = warp_kernel<W, NG>(s->N);
+  const WarpKernel<W> kern = warp_kernel<W, NG>(s->N, use_cta<W>(s));
   int& grid = s->warp_grid[warp_kind<W>() * 8 + NG];
   int& wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
   if (grid != 0) return cudaSuccess;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+  if (use_cta<W>(s)) {                            // fixed warps per CTA, as many CTAs as fit
+    constexpr int C = kCtaWarps;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.warp_bytes);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * C, a.warp_bytes);
+    if (e != cudaSuccess) return e;
+    if (per == 0) return cudaErrorInvalidConfiguration;
+    wpc = C;
+    grid = nsm * per;
+    return cudaSuccess;
+  }
   int best = 0, bw = 1;
   for (int c : {4, 2, 1}) {
     const size_t smem = (size_t)c * a.warp_bytes;
@@ -597,7 +950,9 @@ template <typename W, int NG>
 static cudaError_t launch_warp_ng(stdg_solver* s, const WarpArgs& a, const typename W::XIn* x, typename W::YOut* y) {
   const int grid = s->warp_grid[warp_kind<W>() * 8 + NG], wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
   if (grid == 0) return cudaErrorNotReady;                  // warp_prepare has not run
-  warp_kernel<W, NG>(s->N)<<<grid, 32 * wpc, (size_t)wpc * a.warp_bytes, s->stream>>>(a, x, y);
+  const bool cta = use_cta<W>(s);
+  const size_t smem = cta ? (size_t)a.warp_bytes : (size_t)wpc * a.warp_bytes;
+  warp_kernel<W, NG>(s->N, cta)<<<grid, 32 * wpc, smem, s->stream>>>(a, x, y);
   return cudaGetLastError();
 }
 

@@ -432,13 +432,16 @@ def test_step_with_previous_viscous_solvers():
     assert "2 passed" in r.stdout
 
 
+@pytest.mark.parametrize("kernel", ["tma", "warp"])
+@pytest.mark.parametrize("p,pt", [(3, 1), (4, 4)])
 @pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("df32", 1e-12)])
-def test_tma_operator_kernels_match_oracle(prec, tol, monkeypatch):
-    """STDG_OP_KERNEL=tma selects the block-staged TMA kernels, kept for comparison with the warp
-    kernels: the same operator to the same tolerances (standalone applications; the mixed solvers
-    need the warp kernels' fused p.q partials)."""
-    monkeypatch.setenv("STDG_OP_KERNEL", "tma")
-    gs, d = setup(2, 3, 1, precision=prec)
+def test_alternative_operator_kernels_match_oracle(kernel, p, pt, prec, tol, monkeypatch):
+    """STDG_OP_KERNEL selects the operator kernels kept for comparison with the default one (CTAs of
+    several warps sharing each staged tet): "warp" (one warp per staged tet) and "tma" (block-staged
+    TMA kernels).  The same operator (Eq. CS_19) to the same tolerances as the default kernels, at
+    the benchmarked degrees; the pinned solver of the pressure system, so the pin rows are covered."""
+    monkeypatch.setenv("STDG_OP_KERNEL", kernel)
+    gs, d = setup(2, p, pt, precision=prec)
     x = np.random.default_rng(6).standard_normal(d.mesh.ne * d.Nst)
     if prec == "mixed_f32":
         y = gs.pressure_apply_f32(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
