@@ -55,6 +55,7 @@ struct stdg_solver {
   void *wBv32 = nullptr;                      // the viscous diagonal blocks in binary32 (padded rows)
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
+  int op_cta = 1;                             // with op_warp: several warps share each staged tet
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
@@ -85,6 +86,7 @@ struct stdg_solver {
   double theta = 1.0;                          // semi-implicit pressure weight (p_t = 0 only)
   double *Pn = nullptr, *Pth = nullptr;        // p^n and theta p^{n+1,k} + (1 - theta) p^n (theta < 1)
   float2 *cphiP = nullptr, *cdphiP = nullptr, *cfphiP = nullptr;   // convection tables as (hi, lo) pairs
+  float2 *cphiT = nullptr, *cfphiT = nullptr;                        // the value tables transposed
   float2 *ctgP = nullptr, *ctwP = nullptr;                            // time basis and weights, as pairs
   // device allocations: through the caller's allocator when one was given (stdg_solver_create_alloc),
   // else cudaMalloc; released in reverse order by stdg_solver_destroy
