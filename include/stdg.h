@@ -365,6 +365,17 @@ stdg_status stdg_set_boundary_fn(stdg_solver* s, stdg_vel_fn fn, void* user);
  * be NULL. */
 stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
                       stdg_step_stats* stats);
+/* The convective term alone, step 2 of a Picard iteration (Sec. 2.5, Eq. convdg): for the
+ * velocity averages vbar_dev on the main grid, layout [3][ne][Nst] (component, tet, time column
+ * a, spatial index k at a N + k), writes ups_dev (same layout) with
+ *   Ups^c_i = - int_{T_i x slab} grad(phi~_k) . v_c vbar + int_{dT_i x slab} phi~_k F^RS_c . n_i
+ * on the slab [t, t + dt] that starts at the solver's current time, boundary faces taking the
+ * Dirichlet data of the field set by stdg_set_boundary (Rusanov flux with v+ = v_bc).  Device
+ * buffers owned by the caller; synchronises the solver's stream.  STDG_EUNSUPPORTED when the
+ * boundary data come from a host callback (stdg_set_boundary_fn: evaluated per step only),
+ * STDG_EINVAL on a NULL argument.  STDG_CONV_KERNEL=generic in the environment (read when the
+ * solver is created) selects the runtime-degree kernel at every degree. */
+stdg_status stdg_convection(stdg_solver* s, const double* vbar_dev, double* ups_dev);
 /* Semi-implicit theta variant for p_t = 0 (Sec. 2.7, Eqs. CS_15_theta / CS_16_theta): the
  * momentum of every dual cell sees the pressure as p^{n+theta} = theta p^{n+1} + (1-theta) p^n.
  * stdg_step then takes Lambda (Eq. prevpress) of theta p^{n+1,k} + (1-theta) p^n, solves the

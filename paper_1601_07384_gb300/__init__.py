@@ -335,6 +335,15 @@ class Solver:
         _lib.check(_lib.load().stdg_velocity_moments(self._h, _ptr(V), _ptr(U)))
         return U
 
+    def convection(self, vbar, ups=None):
+        """The convective term of Eq. convdg for velocity averages vbar ([3][ne][Nst] on the device) on
+        the slab starting at the current time, with the boundary field's Dirichlet data."""
+        torch = _torch()
+        vbar = self._dev(vbar)
+        ups = torch.empty(3 * self.ne * self.Nst, dtype=torch.float64, device="cuda") if ups is None else ups
+        _lib.check(_lib.load().stdg_convection(self._h, _ptr(vbar), _ptr(ups)))
+        return ups
+
     # ---------------------------------------------------------------- time stepping
     def set_initial(self, field):
         """Initial velocity: a device field kind (Field), or a host callable fn(x (n, 3), t (n,)) -> (n, 3)

@@ -92,6 +92,7 @@ SIGNATURES = {
     "stdg_get_state": (C.c_int, [P, P, P, C.c_int, DP]),
     "stdg_set_state": (C.c_int, [P, P, P, C.c_int, C.c_double]),
     "stdg_velocity_moments": (C.c_int, [P, P, P]),
+    "stdg_convection": (C.c_int, [P, P, P]),
     "stdg_get_blocks": (C.c_int, [P, DP, DP, DP, DP]),
     "stdg_profile": (C.c_int, [P, C.c_int]),
     "stdg_gnn_init": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_uint64]),

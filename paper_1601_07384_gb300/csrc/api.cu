@@ -82,6 +82,7 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
     const char* k = std::getenv("STDG_OP_KERNEL");
     s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
     s->op_cta = (k && std::strcmp(k, "warp") == 0) ? 0 : 1;
+    s->op_rs = (k && std::strcmp(k, "reg") == 0) ? 1 : 0;
     const char* mi = std::getenv("STDG_MIXED_INNER");   // binary32 iterations per outer mixed step
     if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = s->mix_inner_mg = std::atoi(mi);
     const char* mm = std::getenv("STDG_MIXED_M");       // directions kept by the outer flexible CG
@@ -90,6 +91,8 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
     if (dw && std::atoi(dw) > 0 && std::atoi(dw) <= 64) s->df_min_warps = std::atoi(dw);
     const char* vi = std::getenv("STDG_VISC_INNER64");
     s->visc_inner64 = vi && std::atoi(vi) == 1;
+    const char* ck = std::getenv("STDG_CONV_KERNEL");  // "generic": no compile-time-degree convection kernel
+    s->conv_generic = ck && std::strcmp(ck, "generic") == 0;
   }
   s->p = r->p; s->pt = r->pt; s->N = r->N; s->Ng = r->Ng; s->Nst = r->Nst;
   s->ne = m->ne; s->nf = m->nf; s->nint = m->nint; s->nbd = m->nbd;

@@ -98,6 +98,16 @@ cudaError_t launch_rhs(int ne, int N, int Ng, const int* t2f, const int* left, c
 cudaError_t launch_update(int nf, int N, int Ng, const int* left, const int* right, const double* Q,
                           const double* F, const double* dp, double dt, const double* Kinv,
                           double* V, cudaStream_t st);
+// The support steps in pair arithmetic at the compile-time degrees (support.cu); cudaErrorNotSupported
+// at other (N, Ng), where the binary64 kernels serve.  support_fp64(): STDG_SUPPORT=fp64 in the
+// environment (read once per process) keeps the binary64 kernels everywhere.
+bool support_fp64();
+cudaError_t sup_average(cudaStream_t st, int ne, int N, int Ng, const int* t2f, const int* left, const double* detJ,
+                        const double* Mij, const double* in, double* out);
+cudaError_t sup_face_grad(cudaStream_t st, int nf, int N, int Ng, const int* left, const int* right, const double* Q,
+                          const double* Pp, double dt, const double* Kinv, double* G);
+cudaError_t sup_update(cudaStream_t st, int nf, int N, int Ng, const int* left, const int* right, const double* Q,
+                       const double* F, const double* dp, double dt, const double* Kinv, double* V);
 // U_j[s][c][a][k] = dt Sum_l Mij_s[k][l] V_j[c][a][l]
 cudaError_t launch_moments(int nf, int N, int Ng, const double* Mij, const double* V, double dt,
                            double* U, cudaStream_t st);

@@ -62,7 +62,7 @@ struct PolDF {
     e = (a - (s - bb)) + (b - bb);
   }
   __device__ static void fma(Acc& a, TB b, TZ z) {
-    const float p = b.x * z.x;
+    const float p = __fmul_rn(b.x, z.x);          // never fused into the sum below (error-free TwoSum)
     float e = fmaf(b.x, z.x, -p);
     e = fmaf(b.x, z.y, e);
     e = fmaf(b.y, z.x, e);

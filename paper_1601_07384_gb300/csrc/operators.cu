@@ -191,6 +191,10 @@ __global__ void __launch_bounds__(128) k_update(int N, int Ng, const int* __rest
 cudaError_t launch_update(int nf, int N, int Ng, const int* left, const int* right, const double* Q,
                           const double* F, const double* dp, double dt, const double* Kinv,
                           double* V, cudaStream_t st) {
+  if (nf > 0 && !support_fp64()) {
+    const cudaError_t ep = sup_update(st, nf, N, Ng, left, right, Q, F, dp, dt, Kinv, V);
+    if (ep != cudaErrorNotSupported) return ep;
+  }
   KinvArg k{};
   for (int q = 0; q < Ng * Ng; ++q) k.v[q] = Kinv[q];
   const int Nst = N * Ng;

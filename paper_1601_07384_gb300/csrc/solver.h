@@ -56,11 +56,13 @@ struct stdg_solver {
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
   int op_cta = 1;                             // with op_warp: several warps share each staged tet
+  int op_rs = 0;                              // binary32: blocks streamed from global memory into registers
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps
   int df_min_warps = 3;                       // the pair kernel serves where this many warps fit per SM
   bool visc_inner64 = false;                  // mixed viscous refinement: binary64-vector inner COCG
+  bool conv_generic = false;                  // convection: the runtime-degree kernel at every degree
   double *fcgP = nullptr, *fcgQ = nullptr;    // their P_j and Q_j = S P_j
   double *opdot = nullptr;                    // per-block p.q partials of the binary32 operator launch
   float *lpBinv = nullptr;                    // block-Jacobi inverses in binary32

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "pair.cuh"
 #include "solver.h"
 
 namespace stdg {
@@ -323,42 +324,7 @@ struct ConvArgs {
 // sm_103a's FP64 pipe, which the binary64 kernel kept 86 % busy.  The flux itself (products of the
 // velocities, the Rusanov speed) stays binary64.
 constexpr int kConvCH = 128;        // spatial points per pass (= threads per block)
-
-__device__ __forceinline__ float2 pair_split(double a) {
-  const float h = (float)a;
-  return make_float2(h, (float)(a - (double)h));
-}
-// (s, c) += a b for pairs a, b: TwoProd of the high parts, cross terms into the error, TwoSum into s
-__device__ __forceinline__ void pair_fma(float2 a, float2 b, float& s, float& c) {
-  const float p = a.x * b.x;
-  const float e = fmaf(a.x, b.x, -p);
-  const float t = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
-  const float s2 = s + p;
-  const float bb = s2 - s;
-  c += ((s - (s2 - bb)) + (p - bb)) + t;
-  s = s2;
-}
-__device__ __forceinline__ double pair_value(float s, float c) { return (double)s + (double)c; }
-// (s, c) with |c| small against |s| -> a normalised pair (hi, lo), hi = fl32(s + c) (Fast2Sum)
-__device__ __forceinline__ float2 pair_norm(float s, float c) {
-  const float h = s + c;
-  return make_float2(h, c - (h - s));
-}
-// the product of two pairs as a normalised pair: the high parts' product exactly (FMA), the cross terms
-// into its error
-__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
-  return pair_norm(p, e);
-}
-// a + b and a - b of pairs (TwoSum of the high parts, low parts added to its error)
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-  const float s = a.x + b.x;
-  const float bb = s - a.x;
-  const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
-  return pair_norm(s, e);
-}
-__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+constexpr int kMaxTimePts = 8;      // time points of the compile-time kernels (7 at p_t = 4)
 
 // S[c][b] = Sum_k phi_k(x_q) V[c][b][k] at one quadrature point, as normalised pairs: each basis value
 // is loaded once and used by the 3 Ng sums (the coefficients V are the same for every point: shared
@@ -580,6 +546,312 @@ __global__ void __launch_bounds__(kConvCH) k_convection(ConvArgs a, const float2
   for (int o = threadIdx.x; o < 3 * Nst; o += blockDim.x) {
     const int c = o / Nst, rem = o % Nst;
     a.ups[((size_t)c * ne + i) * Nst + rem] = acc[o];
+  }
+}
+
+// ---- The same convection with N and Ng at compile time (the benchmarked degrees), reorganised:
+//  * points of all four faces go through shared passes of kConvCH (two passes at p = 4 instead of
+//    four passes with 49 of 128 threads busy);
+//  * the test-function sums are owned by threads: thread (c, k) keeps the sums of its time columns
+//    in registers across all passes, so one coalesced table load serves all of them (the general
+//    kernel loads the table once per multiply-add and reads and writes its sums in shared memory);
+//  * the per-point sums Sum_k phi_k(x_q) V[.][k] read the basis tables transposed ([k][point]:
+//    coalesced over the threads of a pass);
+//  * the pair arithmetic of the contractions and of the time folding runs two sums at a time in
+//    packed binary32 operations (f32x2).
+// The arithmetic per term is that of the general kernel (the same products, error terms and
+// error-free sums), so the results agree with it to the rounding of the pair sums.
+
+// S[m] = Sum_k tab[k * stride] V[m * N + k] for the NA coefficient rows of V, as normalised pairs
+template <int N, int NA>
+__device__ __forceinline__ void conv_contract(const float2* __restrict__ tab, int stride, const float2* V,
+                                              float2 (&S)[NA]) {
+  constexpr int NA2 = (NA + 1) / 2;
+  float2 sm[NA2], cm[NA2];
+#pragma unroll
+  for (int m = 0; m < NA2; ++m) sm[m] = cm[m] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+  for (int k = 0; k < N; ++k) {
+    const float2 pk = tab[(size_t)k * stride];
+    const float2 ah2 = make_float2(pk.x, pk.x), nah2 = make_float2(-pk.x, -pk.x), al2 = make_float2(pk.y, pk.y);
+#pragma unroll
+    for (int m = 0; m < NA2; ++m) {
+      const float2 v0 = V[(2 * m) * N + k];
+      const float2 v1 = 2 * m + 1 < NA ? V[(2 * m + 1) * N + k] : make_float2(0.0f, 0.0f);
+      pair_fma2(ah2, nah2, al2, make_float2(v0.x, v1.x), make_float2(v0.y, v1.y), sm[m], cm[m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NA2; ++m) {
+    S[2 * m] = pair_norm(sm[m].x, cm[m].x);
+    if (2 * m + 1 < NA) S[2 * m + 1] = pair_norm(sm[m].y, cm[m].y);
+  }
+}
+
+// G[ta] += h g_ta for the NG time columns of one row of G (NGP pairs, stored (s, c)), packed over
+// consecutive columns; g holds NGP pairs, the padding one zero
+template <int NGP>
+__device__ __forceinline__ void conv_fold(float2* G, float2 h, const float2* g) {
+  const float2 hh2 = make_float2(h.x, h.x), nh2 = make_float2(-h.x, -h.x), hl2 = make_float2(h.y, h.y);
+#pragma unroll
+  for (int m = 0; m < NGP / 2; ++m) {
+    float4 G2 = *reinterpret_cast<float4*>(G + 2 * m);
+    float2 sv = make_float2(G2.x, G2.z), cv = make_float2(G2.y, G2.w);
+    pair_fma2(hh2, nh2, hl2, make_float2(g[2 * m].x, g[2 * m + 1].x), make_float2(g[2 * m].y, g[2 * m + 1].y), sv, cv);
+    *reinterpret_cast<float4*>(G + 2 * m) = make_float4(sv.x, cv.x, sv.y, cv.y);
+  }
+}
+
+template <int N, int NG>
+struct ConvT {
+  static constexpr int Nst = N * NG, NA = 3 * NG, NGP = (NG + 1) & ~1;
+  // owners of the test-function sums: thread -> (split, component c, row k), time columns
+  // [split TG, split TG + TG)
+  static constexpr int NSPLIT = 3 * N * NG <= kConvCH ? NG : 1;
+  static constexpr int TG = NG / NSPLIT, TG2 = (TG + 1) / 2, NOWN = 3 * N * NSPLIT;
+  // shared memory (pairs): own coefficients, then the volume fold G[point][c][e][NGP], which the face
+  // passes reuse for the neighbour coefficients of the four faces and the face fold G[point][c][NGP]
+  // (own coefficients padded to an even count: the folds are read and written as float4)
+  static constexpr int kOwn = (NA * N + 1) & ~1;
+  static constexpr int kVol = kConvCH * 9 * NGP, kFace = 4 * NA * N + kConvCH * 3 * NGP;
+  // then the owners' binary64 sums [NOWN][TG]
+  static constexpr size_t kAccOff = ((size_t)kOwn + (kVol > kFace ? kVol : kFace)) * sizeof(float2);
+  static constexpr size_t kSmem = kAccOff + (size_t)NOWN * TG * sizeof(double);
+};
+
+// the owner's share of Sum_v a_v G_v over the pass: a_v broadcast pair, G rows of the pass
+template <int TG, int NGP>
+__device__ __forceinline__ void conv_owner_acc(float2 av, const float2* G, float2 (&As)[(TG + 1) / 2],
+                                               float2 (&Ac)[(TG + 1) / 2]) {
+  const float2 ah2 = make_float2(av.x, av.x), nah2 = make_float2(-av.x, -av.x), al2 = make_float2(av.y, av.y);
+  if constexpr (TG == 1) {
+    const float2 g = G[0];
+    pair_fma2(ah2, nah2, al2, make_float2(g.x, 0.0f), make_float2(g.y, 0.0f), As[0], Ac[0]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < (TG + 1) / 2; ++m) {
+      const float4 G2 = *reinterpret_cast<const float4*>(G + 2 * m);
+      pair_fma2(ah2, nah2, al2, make_float2(G2.x, G2.z), make_float2(G2.y, G2.w), As[m], Ac[m]);
+    }
+  }
+}
+
+template <int N, int NG>
+__global__ void __launch_bounds__(kConvCH, 3) k_convection_t(ConvArgs a, const float2* __restrict__ phiT,
+                                                             const float2* __restrict__ dphiP,
+                                                             const float2* __restrict__ fphiT,
+                                                             const float2* __restrict__ fphiP) {
+  using C = ConvT<N, NG>;
+  constexpr int Nst = C::Nst, NA = C::NA, NGP = C::NGP, TG = C::TG, TG2 = C::TG2;
+  extern __shared__ float2 cvs[];
+  float2* ViP = cvs;                              // [c][b][k]: own coefficients as pairs
+  float2* Gv = cvs + C::kOwn;                      // volume: [point][c][e][NGP]
+  float2* VnP = Gv;                               // faces: [face][c][b][k] neighbour coefficients
+  float2* Gf = Gv + 4 * NA * N;                   // faces: [point][c][NGP]
+  __shared__ float2 JiP[9];
+  __shared__ float2 fnP[4][3];
+  __shared__ int fjj[4], fnb[4], fcode[4], fcodeb[4];
+  __shared__ float2 gtab[kMaxTimePts * NGP];      // time basis at the time points, padding columns zero
+  const int i = blockIdx.x, u = threadIdx.x, ne = a.ne, nt = a.nt;
+  for (int o = u; o < nt * NGP; o += kConvCH) {
+    const int ti = o / NGP, b = o - ti * NGP;
+    gtab[o] = b < NG ? a.tgP[ti * NG + b] : make_float2(0.0f, 0.0f);
+  }
+  for (int o = u; o < NA * N; o += kConvCH) {
+    const int c = o / Nst, rem = o - c * Nst;
+    ViP[o] = pair_split(a.vbar[((size_t)c * ne + i) * Nst + rem]);
+  }
+  if (u < 9) JiP[u] = pair_split(a.Jinv[9 * (size_t)i + u]);
+  if (u < 4) {
+    const int j = a.t2f[4 * i + u], nb = a.t2n[4 * i + u];
+    const bool me_left = a.left[j] == i;
+    const double sg = me_left ? 1.0 : -1.0;
+    fjj[u] = j; fnb[u] = nb; fcode[u] = a.t2code[4 * i + u];
+    fcodeb[u] = nb >= 0 ? (me_left ? a.code_r[j] : a.code_l[j]) : 0;
+    for (int d = 0; d < 3; ++d) fnP[u][d] = pair_split(sg * a.normal[3 * j + d]);
+  }
+  const bool own = u < C::NOWN;
+  const int osp = u / (3 * N), orem = u - osp * 3 * N, oc = orem / N, ok = orem - oc * N, ota0 = osp * TG;
+  double* accd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cvs) + C::kAccOff) + (size_t)u * TG;
+  if (own)
+#pragma unroll
+    for (int t = 0; t < TG; ++t) accd[t] = 0.0;
+  auto owner_flush = [&](const float2 (&As)[TG2], const float2 (&Ac)[TG2]) {   // a pass's pair sums, in binary64
+#pragma unroll
+    for (int m = 0; m < TG2; ++m) {
+      accd[2 * m] += pair_value(As[m].x, Ac[m].x);
+      if (2 * m + 1 < TG) accd[2 * m + 1] += pair_value(As[m].y, Ac[m].y);
+    }
+  };
+  const double dj = a.detJ[i];
+  __syncthreads();
+
+  // volume term: - int grad(phi~_k) . F_c(vbar)
+  for (int base = 0; base < a.nq; base += kConvCH) {
+    const int cnt = min(kConvCH, a.nq - base);
+    if (u < cnt) {
+      const int q = base + u;
+      float2 S[NA];
+      conv_contract<N, NA>(phiT + q, a.nq, ViP, S);
+      float2* Gu = Gv + (size_t)u * 9 * NGP;
+#pragma unroll
+      for (int e = 0; e < 9 * NGP; e += 2) *reinterpret_cast<float4*>(Gu + e) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float2 wqP = pair_split(a.dt * dj * a.w[q]);
+      for (int ti = 0; ti < nt; ++ti) {
+        const float2* g = gtab + ti * NGP;
+        float2 vP[3], uP[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float ss = 0.0f, cc = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) pair_fma(g[b], S[c * NG + b], ss, cc);
+          vP[c] = pair_norm(ss, cc);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          float ss = 0.0f, cc = 0.0f;
+          pair_fma(JiP[3 * e], vP[0], ss, cc);
+          pair_fma(JiP[3 * e + 1], vP[1], ss, cc);
+          pair_fma(JiP[3 * e + 2], vP[2], ss, cc);
+          uP[e] = pair_norm(ss, cc);
+        }
+        const float2 W = pair_mul(wqP, a.twP[ti]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 Wv = pair_mul(W, vP[c]);
+#pragma unroll
+          for (int e = 0; e < 3; ++e) conv_fold<NGP>(Gu + (c * 3 + e) * NGP, pair_mul(Wv, uP[e]), g);
+        }
+      }
+#pragma unroll 6
+      for (int e = 0; e < 9 * NGP; ++e) Gu[e] = pair_norm(Gu[e].x, Gu[e].y);
+    }
+    __syncthreads();
+    if (own) {
+      float2 As[TG2], Ac[TG2];
+#pragma unroll
+      for (int m = 0; m < TG2; ++m) As[m] = Ac[m] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+      for (int v = 0; v < cnt; ++v) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const float2 dp = dphiP[((size_t)(base + v) * 3 + e) * N + ok];
+          conv_owner_acc<TG, NGP>(make_float2(-dp.x, -dp.y), Gv + ((size_t)v * 9 + oc * 3 + e) * NGP + ota0, As, Ac);
+        }
+      }
+      owner_flush(As, Ac);
+    }
+    __syncthreads();
+  }
+
+  // face terms: + int_{face} phi~_k F^RS . n_i, the points of all four faces in shared passes
+  for (int f = 0; f < 4; ++f) {
+    const int nb = fnb[f];
+    if (nb < 0) continue;
+    for (int o = u; o < NA * N; o += kConvCH) {
+      const int c = o / Nst, rem = o - c * Nst;
+      VnP[f * NA * N + o] = pair_split(a.vbar[((size_t)c * ne + nb) * Nst + rem]);
+    }
+  }
+  __syncthreads();
+  const int nqf = a.nqf, nfp = 4 * nqf;
+  for (int base = 0; base < nfp; base += kConvCH) {
+    const int cnt = min(kConvCH, nfp - base);
+    if (u < cnt) {
+      const int P = base + u, f = P / nqf, q = P - f * nqf;
+      const int j = fjj[f], nb = fnb[f];
+      float2 SmP[NA], SpP[NA];
+      conv_contract<N, NA>(fphiT + (size_t)fcode[f] * N * nqf + q, nqf, ViP, SmP);
+      double x[3] = {0.0, 0.0, 0.0};
+      if (nb >= 0) {
+        conv_contract<N, NA>(fphiT + (size_t)fcodeb[f] * N * nqf + q, nqf, VnP + f * NA * N, SpP);
+      } else {
+        const double* fv = a.fvx + 9 * (size_t)j;
+        const double s0 = a.tri_st[2 * q], t0 = a.tri_st[2 * q + 1];
+        for (int d = 0; d < 3; ++d) x[d] = fv[d] + s0 * (fv[3 + d] - fv[d]) + t0 * (fv[6 + d] - fv[d]);
+      }
+      float2* Gu = Gf + (size_t)u * 3 * NGP;
+#pragma unroll
+      for (int e = 0; e < 3 * NGP; e += 2) *reinterpret_cast<float4*>(Gu + e) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float2 wqP = pair_split(a.dt * 2.0 * a.area[j] * a.tri_w[q]);
+      const float2* nP = fnP[f];
+      for (int ti = 0; ti < nt; ++ti) {
+        const float2* g = gtab + ti * NGP;
+        float2 vm[3], vp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float ss = 0.0f, cc = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NG; ++b) pair_fma(g[b], SmP[c * NG + b], ss, cc);
+          vm[c] = pair_norm(ss, cc);
+        }
+        if (nb >= 0) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float ss = 0.0f, cc = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NG; ++b) pair_fma(g[b], SpP[c * NG + b], ss, cc);
+            vp[c] = pair_norm(ss, cc);
+          }
+        } else {
+          double vb[3];
+          eval_field(a.fld, x, a.t0 + a.ttau[ti] * a.dt,
+                     (int64_t)a.bidx[j] * a.bnpt + (int64_t)a.nq * nt + (int64_t)q * nt + ti, a.ttau[ti], vb);
+          for (int c = 0; c < 3; ++c) vp[c] = pair_split(vb[c]);
+        }
+        // Rusanov flux, s_max = 2 max(|v+|, |v-|) pointwise (the square roots in binary64)
+        float s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f, s3 = 0.0f, c3 = 0.0f, s4 = 0.0f, c4 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pair_fma(vm[c], nP[c], s1, c1);
+          pair_fma(vp[c], nP[c], s2, c2);
+          pair_fma(vm[c], vm[c], s3, c3);
+          pair_fma(vp[c], vp[c], s4, c4);
+        }
+        const float2 unm = pair_norm(s1, c1), unp = pair_norm(s2, c2);
+        const double smax = 2.0 * fmax(sqrt(pair_value(s4, c4)), sqrt(pair_value(s3, c3)));
+        const float2 W = pair_mul(wqP, a.twP[ti]);
+        const float2 hs = pair_mul(W, pair_split(0.5 * smax));
+        const float2 Wh = pair_mul(W, make_float2(0.5f, 0.0f));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          // h = W (0.5 (v+_c un+ + v-_c un-) - 0.5 s_max (v+_c - v-_c))
+          const float2 cen = pair_mul(Wh, pair_add(pair_mul(vp[c], unp), pair_mul(vm[c], unm)));
+          const float2 h = pair_add(cen, pair_neg(pair_mul(hs, pair_add(vp[c], pair_neg(vm[c])))));
+          conv_fold<NGP>(Gu + c * NGP, h, g);
+        }
+      }
+#pragma unroll 6
+      for (int e = 0; e < 3 * NGP; ++e) Gu[e] = pair_norm(Gu[e].x, Gu[e].y);
+    }
+    __syncthreads();
+    if (own) {
+      float2 As[TG2], Ac[TG2];
+#pragma unroll
+      for (int m = 0; m < TG2; ++m) As[m] = Ac[m] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+      for (int v = 0; v < cnt; ++v) {
+        const int P = base + v, f = P / nqf, q = P - f * nqf;
+        const float2 fp = fphiP[((size_t)fcode[f] * nqf + q) * N + ok];
+        conv_owner_acc<TG, NGP>(fp, Gf + ((size_t)v * 3 + oc) * NGP + ota0, As, Ac);
+      }
+      owner_flush(As, Ac);
+    }
+    __syncthreads();
+  }
+  if (own) {
+#pragma unroll
+    for (int t = 0; t < TG; ++t) a.ups[((size_t)oc * ne + i) * Nst + (ota0 + t) * N + ok] = accd[t];
+  }
+}
+
+// tables transposed per block: out[b][c][r] = pair(in[b][r][c]) for nb blocks of R x C
+__global__ void k_split_pairs_t(int64_t nb, int R, int C, const double* __restrict__ in, float2* __restrict__ out) {
+  const int64_t per = (int64_t)R * C;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per;
+    const int rem = (int)(e - b * per), c = rem / R, r = rem - c * R;
+    out[e] = pair_split(in[b * per + (int64_t)r * C + c]);
   }
 }
 
@@ -853,6 +1125,77 @@ extern "C" stdg_status stdg_set_theta(stdg_solver* s, double theta) {
   return STDG_OK;
 }
 
+// Ups = the convective term of Eq. convdg for the velocity averages vbar ([3][ne][Nst]) on the slab
+// starting at s->t (boundary data of the current boundary field or callback table); builds the pair
+// tables on first use.  Launches on s->stream.
+static stdg_status convection(stdg_solver* s, const double* vbar, double* ups) {
+  const int N = s->N, Ng = s->Ng, Nst = s->Nst, ne = (int)s->ne;
+  cudaStream_t st = s->stream;
+  stdg_status e;
+  const size_t conv_smem = ((size_t)9 * Nst + (size_t)kConvCH * 9 * Ng) * sizeof(double);
+  // compile-time kernels for the benchmarked degrees (p = 3, p_t = 1 and p = p_t = 4)
+  const int conv_t = s->conv_generic || s->nt_nl > kMaxTimePts ? 0
+                     : (N == 35 && Ng == 5)                    ? 1
+                     : (N == 20 && Ng == 2)                    ? 2
+                                                               : 0;
+  if (conv_t == 1)
+    cudaFuncSetAttribute(k_convection_t<35, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ConvT<35, 5>::kSmem);
+  else if (conv_t == 2)
+    cudaFuncSetAttribute(k_convection_t<20, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ConvT<20, 2>::kSmem);
+  else
+    cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+  if (!s->cphiP) {                                  // the convection tables as binary32 pairs, once
+    const size_t n1 = (size_t)s->nq_nl * N, n2 = (size_t)s->nq_nl * 3 * N, n3 = (size_t)64 * s->nqf_nl * N;
+    const size_t n4 = (size_t)s->nt_nl * Ng, n5 = (size_t)s->nt_nl;
+    if ((e = dev_alloc(s, (void**)&s->cphiP, (2 * n1 + n2 + 2 * n3 + n4 + n5) * sizeof(float2))) != STDG_OK) return e;
+    s->cdphiP = s->cphiP + n1;
+    s->cfphiP = s->cdphiP + n2;
+    s->ctgP = s->cfphiP + n3;
+    s->ctwP = s->ctgP + n4;
+    s->cphiT = s->ctwP + n5;                        // transposed copies: [k][point], [code][k][point]
+    s->cfphiT = s->cphiT + n1;
+    s->nlaunch += 7;
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n1, s->dr.tet_nl_phi, s->cphiP);
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n2, s->dr.tet_nl_dphi, s->cdphiP);
+    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n3, s->dr.face_nl_phi, s->cfphiP);
+    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n4, s->d_tg, s->ctgP);
+    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n5, s->d_tw, s->ctwP);
+    k_split_pairs_t<<<256, 256, 0, st>>>(1, s->nq_nl, N, s->dr.tet_nl_phi, s->cphiT);
+    k_split_pairs_t<<<256, 256, 0, st>>>(64, s->nqf_nl, N, s->dr.face_nl_phi, s->cfphiT);
+  }
+  ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
+              s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
+              s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
+              s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, bc_arg(s), s->t, s->dt, s->ctgP, s->ctwP, s->bidx,
+              (s->nq_nl + s->nqf_nl) * s->nt_nl, vbar, ups};
+  if (conv_t == 1)
+    k_convection_t<35, 5><<<ne, kConvCH, ConvT<35, 5>::kSmem, st>>>(ca, s->cphiT, s->cdphiP, s->cfphiT, s->cfphiP);
+  else if (conv_t == 2)
+    k_convection_t<20, 2><<<ne, kConvCH, ConvT<20, 2>::kSmem, st>>>(ca, s->cphiT, s->cdphiP, s->cfphiT, s->cfphiP);
+  else
+    k_convection<<<ne, kConvCH, conv_smem, st>>>(ca, s->cphiP, s->cdphiP, s->cfphiP);
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) { set_error("convection launch failed: %s", cudaGetErrorString(ce)); return STDG_ECUDA; }
+  return STDG_OK;
+}
+
+// averaging and face gradient: the pair-arithmetic kernels (support.cu) at the compile-time degrees,
+// the binary64 ones above otherwise (the go back and the pressure right-hand side stay binary64)
+static void step_average(stdg_solver* s, const double* in, double* out) {
+  const int ne = (int)s->ne, N = s->N, Ng = s->Ng;
+  if (!support_fp64() &&
+      sup_average(s->stream, ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, in, out) != cudaErrorNotSupported)
+    return;
+  k_average<<<ne, 128, 0, s->stream>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, in, out);
+}
+static void step_face_grad(stdg_solver* s, const double* P, MArg Ki, double* G) {
+  const int nf = (int)s->nf, N = s->N, Ng = s->Ng, Nst = s->Nst;
+  if (!support_fp64() && sup_face_grad(s->stream, nf, N, Ng, s->dm.left, s->dm.right, s->Q, P, s->dt, s->Kinv.data(),
+                                       G) != cudaErrorNotSupported)
+    return;
+  k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), s->stream>>>(N, Ng, s->dm.left, s->dm.right, s->Q, P, s->dt, Ki, G);
+}
+
 extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int method, double tol,
                                  stdg_step_stats* stats) {
   if (!s || n_picard < 1 || n_picard > 8 || !(tol > 0.0) || nu < 0.0) { set_error("stdg_step: invalid argument"); return STDG_EINVAL; }
@@ -873,7 +1216,7 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   phase_mark(s, -1);
   // previous slab average and new-slab boundary data
   ++s->nlaunch;
-  k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar_n);
+  step_average(s, s->V, s->Vbar_n);
   if ((e = boundary_data(s, s->t)) != STDG_OK) return e;
   // step 0: v^{n+1,0}(x, tau) = v^n(x, 1), p^{n+1,0} = 0
   ++s->nlaunch;
@@ -886,28 +1229,11 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
     cudaMemcpyAsync(s->Pn, s->P, np * sizeof(double), cudaMemcpyDeviceToDevice, st);
   }
   cudaMemsetAsync(s->P, 0, np * sizeof(double), st);
-  const size_t conv_smem = ((size_t)9 * Nst + (size_t)kConvCH * 9 * Ng) * sizeof(double);
-  cudaFuncSetAttribute(k_convection, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
-  if (!s->cphiP) {                                  // the convection tables as binary32 pairs, once
-    const size_t n1 = (size_t)s->nq_nl * N, n2 = (size_t)s->nq_nl * 3 * N, n3 = (size_t)64 * s->nqf_nl * N;
-    const size_t n4 = (size_t)s->nt_nl * Ng, n5 = (size_t)s->nt_nl;
-    if ((e = dev_alloc(s, (void**)&s->cphiP, (n1 + n2 + n3 + n4 + n5) * sizeof(float2))) != STDG_OK) return e;
-    s->cdphiP = s->cphiP + n1;
-    s->cfphiP = s->cdphiP + n2;
-    s->ctgP = s->cfphiP + n3;
-    s->ctwP = s->ctgP + n4;
-    s->nlaunch += 5;
-    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n1, s->dr.tet_nl_phi, s->cphiP);
-    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n2, s->dr.tet_nl_dphi, s->cdphiP);
-    k_split_pairs<<<256, 256, 0, st>>>((int64_t)n3, s->dr.face_nl_phi, s->cfphiP);
-    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n4, s->d_tg, s->ctgP);
-    k_split_pairs<<<1, 64, 0, st>>>((int64_t)n5, s->d_tw, s->ctwP);
-  }
   phase_mark(s, 0);
   for (int k = 0; k < n_picard; ++k) {
     // 1. averaging and previous-Picard pressure gradient
     ++s->nlaunch;
-    k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->V, s->Vbar);
+    step_average(s, s->V, s->Vbar);
     // Lambda of Eq. prevpress, of p^{n+theta,k} = theta p^{n+1,k} + (1 - theta) p^n (Eq. CS_16_theta)
     const double* Plam = s->P;
     if (th != 1.0) {
@@ -916,18 +1242,13 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
       Plam = s->Pth;
     }
     ++s->nlaunch;
-    k_face_grad<<<nf, 128, 3 * Nst * sizeof(double), st>>>(N, Ng, s->dm.left, s->dm.right, s->Q, Plam, s->dt, Ki, s->F);
+    step_face_grad(s, Plam, Ki, s->F);
     ++s->nlaunch;
-    k_average<<<ne, 128, 0, st>>>(ne, N, Ng, s->dm.t2f, s->dm.left, s->dm.detJ, s->Mij, s->F, s->Lam);
+    step_average(s, s->F, s->Lam);
     phase_mark(s, 1);
     // 2. convection
-    ConvArgs ca{ne, N, Ng, s->nq_nl, s->nqf_nl, s->nt_nl, s->dm.t2f, s->dm.t2n, s->dm.t2code, s->dm.left,
-                s->dm.code_l, s->dm.code_r, s->dm.detJ, s->dm.Jinv, s->dm.normal, s->dm.area, s->dm.fvx,
-                s->dr.tet_nl_phi, s->dr.tet_nl_dphi, s->dr.tet_nl_w, s->dr.face_nl_phi, s->dr.tri_nl_st,
-                s->dr.tri_nl_w, s->d_ttau, s->d_tw, s->d_tg, bc_arg(s), s->t, s->dt, s->ctgP, s->ctwP, s->bidx,
-                (s->nq_nl + s->nqf_nl) * s->nt_nl, s->Vbar, s->Ups};
     ++s->nlaunch;
-    k_convection<<<ne, kConvCH, conv_smem, st>>>(ca, s->cphiP, s->cdphiP, s->cfphiP);
+    if ((e = convection(s, s->Vbar, s->Ups)) != STDG_OK) return e;
     phase_mark(s, 2);
     // 3. viscous systems (Eq. A1_mod), one per component, initial guess vbar^{n+1,k}
     ++s->nlaunch;
@@ -991,5 +1312,22 @@ extern "C" stdg_status stdg_step(stdg_solver* s, double nu, int n_picard, int me
   s->t += s->dt;
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = local;
+  return STDG_OK;
+}
+
+// The convective term alone (Eq. convdg) for given velocity averages, on the slab that starts at the
+// solver's current time.
+extern "C" stdg_status stdg_convection(stdg_solver* s, const double* vbar, double* ups) {
+  if (!s || !vbar || !ups) { set_error("stdg_convection: NULL argument"); return STDG_EINVAL; }
+  if (s->bc_fn) { set_error("stdg_convection: the boundary data come from a host callback (evaluated per step only)"); return STDG_EUNSUPPORTED; }
+  cudaSetDevice(s->device);
+  stdg_status e = ensure_step(s);
+  if (e != STDG_OK) return e;
+  ++s->nlaunch;
+  if ((e = convection(s, vbar, ups)) != STDG_OK) return e;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    set_error("stdg_convection: %s", cudaGetErrorString(cudaGetLastError()));
+    return STDG_ECUDA;
+  }
   return STDG_OK;
 }

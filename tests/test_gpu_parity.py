@@ -432,13 +432,13 @@ def test_step_with_previous_viscous_solvers():
     assert "2 passed" in r.stdout
 
 
-@pytest.mark.parametrize("kernel", ["tma", "warp"])
+@pytest.mark.parametrize("kernel", ["tma", "warp", "reg"])
 @pytest.mark.parametrize("p,pt", [(3, 1), (4, 4)])
 @pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("df32", 1e-12)])
 def test_alternative_operator_kernels_match_oracle(kernel, p, pt, prec, tol, monkeypatch):
-    """STDG_OP_KERNEL selects the operator kernels kept for comparison with the default one (CTAs of
-    several warps sharing each staged tet): "warp" (one warp per staged tet) and "tma" (block-staged
-    TMA kernels).  The same operator (Eq. CS_19) to the same tolerances as the default kernels, at
+    """STDG_OP_KERNEL selects the operator kernels kept for comparison with the default ones: "warp"
+    (one warp per staged tet, also for the pair policy at N = 35), "reg" (binary32 blocks streamed
+    from global memory into registers) and "tma" (block-staged TMA kernels).  The same operator (Eq. CS_19) to the same tolerances as the default kernels, at
     the benchmarked degrees; the pinned solver of the pressure system, so the pin rows are covered."""
     monkeypatch.setenv("STDG_OP_KERNEL", kernel)
     gs, d = setup(2, p, pt, precision=prec)
@@ -526,6 +526,32 @@ def test_mixed_viscous_inner_solves_match_oracle(p, pt, npic, inner64, monkeypat
     ev = rel(_moments(gs, d, V), Uo)
     print(f"p={p} pt={pt} inner64={inner64}: pressure {ep:.2e} velocity {ev:.2e} visc iters {st['visc_iters']}")
     assert ep <= STEP_TOL and ev <= STEP_TOL
+
+
+@pytest.mark.parametrize("p,pt", [(3, 1), (4, 4), (2, 2), (4, 1)])
+@pytest.mark.parametrize("kernel", ["default", "generic"])
+def test_convection_matches_oracle(p, pt, kernel, monkeypatch):
+    """The convective term alone (Eq. convdg: the volume integral of grad(phi~) . v vbar and the
+    Rusanov face fluxes, Beltrami Dirichlet data on the boundary faces) for seeded random velocity
+    averages, element by element against the oracle's, with the compile-time-degree kernels (the
+    default at (p, p_t) = (3, 1) and (4, 4)) and with the runtime-degree kernel
+    (STDG_CONV_KERNEL=generic).  Both evaluate every product and sum binary64-accurately."""
+    import paper_1601_07384_gb300 as g
+    if kernel == "generic":
+        monkeypatch.setenv("STDG_CONV_KERNEL", "generic")
+    nu, dt = 0.1, 0.01
+    prm = BeltramiParams(nu=nu)
+    gs, d = setup(2, p, pt, dt=dt)
+    gs.set_boundary(g.beltrami(prm.a, prm.d, prm.nu))
+    ne, Nst = d.mesh.ne, d.Nst
+    vbar = np.random.default_rng(17).standard_normal((ne, 3, Nst)) * 0.3
+    ups = gs.convection(torch.from_numpy(np.ascontiguousarray(vbar.transpose(1, 0, 2))).cuda())
+    ups = ups.cpu().numpy().reshape(3, ne, Nst).transpose(1, 0, 2)
+    uo = ops.convection(d, vbar, 0.0, lambda x, tt: beltrami_velocity(x, tt, prm))
+    err = rel(ups, uo)
+    where = np.unravel_index(np.abs(ups - uo).argmax(), ups.shape)
+    print(f"p={p} pt={pt} {kernel}: max rel {err:.2e} at (tet, c, st) = {where}")
+    assert err <= 1e-12
 
 
 @pytest.mark.parametrize("tol,bound", [(1e-13, STEP_TOL), (1e-12, 1e-8)])
