@@ -763,188 +763,6 @@ __global__ void __launch_bounds__(32 * WPC) k_apply_cta(WarpArgs a, const typena
   }
 }
 
-// binary32 blocks read straight from global memory into registers (no shared-memory stage for the
-// blocks): one warp per tet, persistent.  Only the x rows of the tet and its neighbours are staged,
-// per warp, in two buffers filled by cp.async groups, the next tet's while this one computes.  Row k
-// of a block read by rows: lane k's 16-byte loads along its row (two loads per 32-byte sector, the
-// second served by L1); a block read by columns (A_rl = A_lr^T): one 128-byte coalesced load per
-// block row across the lanes.  The products, rows 32..N-1 and the row epilogue are the warp kernel's.
-template <int NG, int NC>
-__global__ void __launch_bounds__(128) k_apply_rs(WarpArgs a, const float* __restrict__ x, float* __restrict__ y) {
-  constexpr int N = NC, NR = warp_nr_c(NC), NP = warp_np_c(NC), Nst = NC * NG, ZR = 5 * NG * NR;
-  extern __shared__ __align__(16) float rsm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  float* zst = rsm + (size_t)warp * 2 * ZR;      // two x buffers [slot][q][NR]
-  const float scale = (float)a.scale;
-  const bool has_mass = a.mass_coef != 0.0, kron = a.kron != 0, pinned = a.pinned != 0;
-  float tacc[NG * NG], kmass[NG * NG];
-#pragma unroll
-  for (int c = 0; c < NG * NG; ++c) { tacc[c] = (float)a.Tacc[c]; kmass[c] = (float)a.Kmass[c]; }
-  for (int e = lane; e < 2 * ZR; e += 32) zst[e] = 0.0f;   // padding entries stay 0
-  __syncwarp();
-  const float* Bd = static_cast<const float*>(a.Bd);
-  const float* Ao = static_cast<const float*>(a.Ao);
-  constexpr int kBlk = NR * NP;
-  auto stage_x = [&](int i, float* zb) {
-    const int4 gf = a.gface[i], gn = a.gnbr[i];
-    for (int idx = lane; idx < 5 * NG * N; idx += 32) {
-      const int rw = idx / N, l = idx - rw * N, sl = rw / NG;
-      const int nb = slot_tet(i, sl, gf, gn);
-      if (nb >= 0) cp_async<4>(zb + rw * NR + l, x + (size_t)nb * Nst + (rw - sl * NG) * N + l);
-    }
-    cp_async_commit();
-  };
-  const int nw = gridDim.x * wpc;
-  float dacc[NG];
-#pragma unroll
-  for (int q = 0; q < NG; ++q) dacc[q] = 0.0f;
-  int i = blockIdx.x * wpc + warp, it = 0;
-  if (i < a.ne) stage_x(i, zst);
-  for (; i < a.ne; i += nw, ++it) {
-    float* zb = zst + (it & 1) * ZR;
-    if (i + nw < a.ne) stage_x(i + nw, zst + ((it + 1) & 1) * ZR);
-    else cp_async_commit();                       // an empty group keeps the count uniform
-    cp_async_wait<1>();                           // this tet's rows (this lane's copies)
-    __syncwarp();
-    const int4 gf = a.gface[i], gn = a.gnbr[i];
-    if (pinned && lane < 5 * NG) {                // pinned entries (constant mode of tet 0) read as 0
-      if (slot_tet(i, lane / NG, gf, gn) == 0) zb[lane * NR] = 0.0f;
-    }
-    __syncwarp();
-    const int fj[4] = {gf.x, gf.y, gf.z, gf.w};
-    auto block_ptr = [&](int sl) -> const float* {
-      return sl == 0 ? Bd + (size_t)i * kBlk : Ao + (size_t)(pick4(gf, sl - 1) >> 1) * kBlk;
-    };
-    auto finish = [&](int k, const float (&v)[NG]) {
-#pragma unroll
-      for (int q = 0; q < NG; ++q) {
-        float o = v[q];
-        if (!kron) {
-          o = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NG; ++b) o += tacc[q * NG + b] * v[b];
-        }
-        o *= scale;
-        if (has_mass) {
-          float m = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NG; ++b) m += kmass[q * NG + b] * zb[b * NR + k];
-          o += (float)(a.mass_coef * a.detJ[i]) * m;
-        }
-        if (pinned && i == 0 && k == 0) o = (float)a.pin_diag * x[q * N];
-        y[(size_t)i * Nst + q * N + k] = o;
-        if (a.dotpart) dacc[q] += x[(size_t)i * Nst + q * N + k] * o;
-      }
-    };
-    if (lane < (N < 32 ? N : 32)) {
-      const int k = lane;
-      float2 c0[NG], c1[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) c0[q] = c1[q] = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int sl = 0; sl < 5; ++sl) {
-        if (sl > 0 && fj[sl - 1] < 0) continue;
-        const float* B = block_ptr(sl);
-        const float* z = zb + sl * NG * NR;
-        if (sl == 0 || !(fj[sl - 1] & 1)) {       // row k: 16-byte loads along the row
-          const float4* Br = reinterpret_cast<const float4*>(B + k * NP);
-          float4 bv[NR / 4];
-#pragma unroll
-          for (int m = 0; m < NR / 4; ++m) bv[m] = __ldg(Br + m);
-#pragma unroll
-          for (int m = 0; m < NR / 4; ++m) {
-            const float2 b01 = make_float2(bv[m].x, bv[m].y), b23 = make_float2(bv[m].z, bv[m].w);
-#pragma unroll
-            for (int q = 0; q < NG; ++q) {
-              const float4 zv = *reinterpret_cast<const float4*>(z + q * NR + 4 * m);
-              float2& acc = (m & 1) ? c1[q] : c0[q];
-              acc = __ffma2_rn(b01, make_float2(zv.x, zv.y), acc);
-              acc = __ffma2_rn(b23, make_float2(zv.z, zv.w), acc);
-            }
-          }
-        } else {                                  // column k: one coalesced load per block row
-          float bc[NR];
-#pragma unroll
-          for (int l = 0; l < NR; ++l) bc[l] = __ldg(B + l * NP + k);
-#pragma unroll
-          for (int m = 0; m < NR / 4; ++m) {
-            const float2 b01 = make_float2(bc[4 * m], bc[4 * m + 1]), b23 = make_float2(bc[4 * m + 2], bc[4 * m + 3]);
-#pragma unroll
-            for (int q = 0; q < NG; ++q) {
-              const float4 zv = *reinterpret_cast<const float4*>(z + q * NR + 4 * m);
-              float2& acc = (m & 1) ? c1[q] : c0[q];
-              acc = __ffma2_rn(b01, make_float2(zv.x, zv.y), acc);
-              acc = __ffma2_rn(b23, make_float2(zv.z, zv.w), acc);
-            }
-          }
-        }
-      }
-      float v[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) v[q] = (c0[q].x + c0[q].y) + (c1[q].x + c1[q].y);
-      finish(k, v);
-    }
-    if (N > 32) {                                 // rows 32 .. N-1: 8 lanes per row, chunks split
-      const int g = lane >> 3, c = lane & 7, r = 32 + g;
-      float2 ec[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) ec[q] = make_float2(0.0f, 0.0f);
-      if (r < N) {
-#pragma unroll
-        for (int sl = 0; sl < 5; ++sl) {
-          if (sl > 0 && fj[sl - 1] < 0) continue;
-          const float* B = block_ptr(sl);
-          const float* z = zb + sl * NG * NR;
-          const bool tr = sl > 0 && (fj[sl - 1] & 1);
-          for (int ch = c; ch < NR / 4; ch += 8) {
-            const int l = 4 * ch;
-            float b[4];
-            if (!tr) {
-              const float4 bv = __ldg(reinterpret_cast<const float4*>(B + r * NP + l));
-              b[0] = bv.x; b[1] = bv.y; b[2] = bv.z; b[3] = bv.w;
-            } else {
-#pragma unroll
-              for (int u = 0; u < 4; ++u) b[u] = __ldg(B + (l + u) * NP + r);
-            }
-#pragma unroll
-            for (int q = 0; q < NG; ++q) {
-              const float4 zv = *reinterpret_cast<const float4*>(z + q * NR + l);
-              ec[q] = __ffma2_rn(make_float2(b[0], b[1]), make_float2(zv.x, zv.y), ec[q]);
-              ec[q] = __ffma2_rn(make_float2(b[2], b[3]), make_float2(zv.z, zv.w), ec[q]);
-            }
-          }
-        }
-      }
-      float v[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) {
-        float h = ec[q].x + ec[q].y;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-        v[q] = h;
-      }
-      if (c == 0 && r < N) finish(r, v);
-    }
-    __syncwarp();                                 // this buffer is refilled two tets later
-  }
-  cp_async_wait<0>();
-  if (a.dotpart) {                                // fixed order: lanes by shuffle, warps by index
-    __shared__ float wdot[4][kMaxNg];
-#pragma unroll
-    for (int q = 0; q < NG; ++q) {
-      float v = dacc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wdot[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NG) {
-      double t = 0.0;
-      for (int w = 0; w < wpc; ++w) t += (double)wdot[w][threadIdx.x];
-      a.dotpart[(size_t)blockIdx.x * NG + threadIdx.x] = t;
-    }
-  }
-}
-
 // padded block copies: dst block b = planes x NR x NP, zero outside N x N
 template <typename TB, int PLANES>
 __global__ void k_to_padded(int64_t nblk, int N, int NR, int NP, const double* __restrict__ src, TB* __restrict__ dst,
@@ -1035,13 +853,6 @@ constexpr int kCtaWarps = 4;
 // share among warps (N = 35: 19.2 -> 11.7 ms per application at 384,000 tets, the warp kernel fitting
 // three warps per SM); for the binary32 policies and at N <= 20 the per-tet work is too short for
 // three CTA barriers and the serial row pass (measured 1.4-2x slower), so the warp kernels serve.
-// register-streaming binary32 kernel (STDG_OP_KERNEL=reg) at N = 20 and 35
-template <typename W>
-static bool use_rs(const stdg_solver* s) {
-  return s->op_rs != 0 && W::kPlanes == 1 && sizeof(typename W::TB) == 4 && (s->N == 20 || s->N == 35);
-}
-static size_t rs_smem(const stdg_solver* s) { return (size_t)4 * 2 * 5 * s->Ng * warp_nr(s->N) * sizeof(float); }
-
 template <typename W>
 static bool use_cta(const stdg_solver* s) {
   return s->op_cta != 0 && W::kPlanes == 2 && s->N > 20;
@@ -1067,8 +878,6 @@ static constexpr int warp_kind() { return W::kPlanes == 2 ? 2 : (sizeof(typename
 
 template <typename W>
 using WarpKernel = void (*)(WarpArgs, const typename W::XIn*, typename W::YOut*);
-template <int NG>
-static WarpKernel<WF32> rs_kernel(int N) { return N == 35 ? k_apply_rs<NG, 35> : k_apply_rs<NG, 20>; }
 
 // the instantiation for this N: compile-time N for p = 2, 3, 4, runtime N otherwise (CTA kernels:
 // pair policy only, see use_cta)
@@ -1096,18 +905,6 @@ static cudaError_t warp_configure(stdg_solver* s) {
   if (grid != 0) return cudaSuccess;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
-  if constexpr (W::kPlanes == 1 && sizeof(typename W::TB) == 4) {
-    if (use_rs<W>(s)) {
-      const WarpKernel<WF32> rk = rs_kernel<NG>(s->N);
-      int per = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rk, 128, rs_smem(s));
-      if (e != cudaSuccess) return e;
-      if (per == 0) return cudaErrorInvalidConfiguration;
-      wpc = 4;
-      grid = nsm * per;
-      return cudaSuccess;
-    }
-  }
   if (use_cta<W>(s)) {                            // fixed warps per CTA, as many CTAs as fit
     constexpr int C = kCtaWarps;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.warp_bytes);
@@ -1153,12 +950,6 @@ template <typename W, int NG>
 static cudaError_t launch_warp_ng(stdg_solver* s, const WarpArgs& a, const typename W::XIn* x, typename W::YOut* y) {
   const int grid = s->warp_grid[warp_kind<W>() * 8 + NG], wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
   if (grid == 0) return cudaErrorNotReady;                  // warp_prepare has not run
-  if constexpr (W::kPlanes == 1 && sizeof(typename W::TB) == 4) {
-    if (use_rs<W>(s)) {
-      rs_kernel<NG>(s->N)<<<grid, 128, rs_smem(s), s->stream>>>(a, x, y);
-      return cudaGetLastError();
-    }
-  }
   const bool cta = use_cta<W>(s);
   const size_t smem = cta ? (size_t)a.warp_bytes : (size_t)wpc * a.warp_bytes;
   warp_kernel<W, NG>(s->N, cta)<<<grid, 32 * wpc, smem, s->stream>>>(a, x, y);
