@@ -6,8 +6,9 @@
 // binary32 multiply-adds per entry instead of Ng binary64 ones.  The inner solve is asked for a
 // residual reduction of 1e-5, well inside binary32 rounding; the binary64 outer refinement forms its
 // residual with the binary64-accurate operator, so the rounding here changes the number of outer steps,
-// not the accuracy of the result.  Partial sums are binary32 over a thread's few dozen rows, then
-// binary64 across threads and blocks in a fixed order (results repeat bit for bit).
+// not the accuracy of the result.  Partial sums are binary32 over a thread's few dozen rows and across
+// the lanes of a warp, then binary64 across warps and blocks, in a fixed order (results repeat bit for
+// bit).
 #include "solver.h"
 
 namespace stdg {
@@ -16,7 +17,9 @@ namespace {
 constexpr int kC32Blocks = 1216;    // 8 x 152 SMs
 constexpr int kC32Threads = 256;
 
-__device__ __forceinline__ double c32_warp_sum(double v) {
+// warp sum in binary32 (binary64 shuffle-adds would cost FP64-pipe time per thread on sm_103a)
+__device__ __forceinline__ float c32_warp_sum_f(float v) {
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
@@ -93,10 +96,10 @@ __global__ void __launch_bounds__(kC32Threads) k_c32_cross(int ne, int N, const 
   __shared__ double red[3 * NG][kC32Threads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int a = 0; a < NG; ++a) {
-    const double sd = c32_warp_sum((double)cd[a]);
-    const double su = c32_warp_sum((double)cu[a]);
-    const double sl = c32_warp_sum((double)cl[a]);
+  for (int a = 0; a < NG; ++a) {                  // binary32 within the warp, binary64 across warps
+    const float sd = c32_warp_sum_f(cd[a]);
+    const float su = c32_warp_sum_f(cu[a]);
+    const float sl = c32_warp_sum_f(cl[a]);
     if (lane == 0) { red[3 * a][w] = sd; red[3 * a + 1][w] = su; red[3 * a + 2][w] = sl; }
   }
   __syncthreads();
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kC32Threads) k_c32_update(int ne, int N, const
   }
   if (!want) return;                              // uniform over the grid
   __shared__ double red[kC32Threads / 32];
-  const double s = c32_warp_sum((double)acc);
+  const double s = (double)c32_warp_sum_f(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {

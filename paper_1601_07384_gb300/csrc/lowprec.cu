@@ -455,12 +455,20 @@ __device__ inline double lp_warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ inline void lp_block_store(double* v, int cnt, double* part, int stride) {
+// Block-reduce `cnt` binary32 per-thread partials (cnt <= 8) into part[blockIdx.x * stride + c]: binary32
+// within a warp (five shuffle-adds; binary64 ones would cost 5 cnt FP64-pipe operations per thread, tens
+// of microseconds per launch on sm_103a), binary64 across the warps, in a fixed order.
+template <int MAXC>
+__device__ inline void lp_block_store(const float (&v)[MAXC], int cnt, double* part, int stride) {
   __shared__ double red[8][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = 0; c < cnt; ++c) {
-    double t = lp_warp_sum(v[c]);
-    if (lane == 0) red[c][w] = t;
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    if (c >= cnt) break;
+    float t = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) red[c][w] = (double)t;
   }
   __syncthreads();
   if (threadIdx.x < cnt) {
@@ -481,9 +489,7 @@ __global__ void __launch_bounds__(256) k_lp_coldot(int64_t ne, int N, int Ng, co
     const int64_t o = i * Nst + (e - i * N);
     for (int a = 0; a < Ng; ++a) acc[a] = fmaf(x[o + a * N], y[o + a * N], acc[a]);
   }
-  double d[8];
-  for (int a = 0; a < 8; ++a) d[a] = acc[a];
-  lp_block_store(d, Ng, part, Ng);
+  lp_block_store(acc, Ng, part, Ng);
 }
 struct LpTp { float v[kMaxNg * kMaxNg]; };
 // x += alpha_a p; r -= alpha_a q; with want, partials of r.r per column and of ||(I (x) Tp) r||^2
@@ -515,9 +521,7 @@ __global__ void __launch_bounds__(256) k_lp_cg_update(int64_t ne, int N, int Ng,
       }
   }
   if (!want) return;
-  double d[8];
-  for (int a = 0; a < 8; ++a) d[a] = acc[a];
-  lp_block_store(d, Ng + 1, part, Ng + 1);
+  lp_block_store(acc, Ng + 1, part, Ng + 1);
 }
 __global__ void k_lp_cg_dir(int64_t ne, int N, int Ng, const double* __restrict__ beta, const float* __restrict__ z,
                             float* __restrict__ p) {
@@ -571,9 +575,7 @@ __global__ void __launch_bounds__(256) k_lp_bjacobi(int ne, int Nrt, int Ng, con
     }
   }
   __syncthreads();
-  double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int a = 0; a < kMaxNg; ++a) d[a] = acc[a];
-  lp_block_store(d, Ng, part, Ng);
+  lp_block_store(acc, Ng, part, Ng);
 }
 // The update and the preconditioner of one binary32 CG iteration in one pass: x += alpha_a p,
 // r -= alpha_a q (alpha from the device), then z = Binv r from the updated rows kept in shared
@@ -645,10 +647,7 @@ __global__ void __launch_bounds__(256) k_lp_update_bj(int ne, int Nrt, int Ngrt,
     }
   }
   __syncthreads();
-  double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-  for (int a = 0; a < NGM; ++a) d[a] = acc[a];
-  lp_block_store(d, Ng, part, Ng);
+  lp_block_store(acc, Ng, part, Ng);
 }
 
 void lp_update_bjacobi(cudaStream_t st, int ne, int N, int Ng, const double* alpha, float* x, float* r, const float* p,

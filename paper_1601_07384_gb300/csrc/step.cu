@@ -946,6 +946,12 @@ static stdg_status ensure_step(stdg_solver* s) {
 }
 
 static cudaError_t launch_boundary(stdg_solver* s, double t0, const FieldArg& fld) {
+  if (fld.kind == STDG_FIELD_ZERO) {               // no-slip walls: every projection is exactly 0
+    const size_t nv = (size_t)s->nf * 3 * s->Nst * sizeof(double);
+    cudaMemsetAsync(s->Vbc, 0, nv, s->stream);
+    cudaMemsetAsync(s->Gbc, 0, 3 * nv, s->stream);
+    return cudaGetLastError();
+  }
   const int CH = 64;
   size_t smem = ((size_t)CH * s->N * 2 + CH * 3) * sizeof(double);
   cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
