@@ -82,7 +82,6 @@ static stdg_status solver_create(const stdg_mesh* m, const stdg_ref* r, double d
     const char* k = std::getenv("STDG_OP_KERNEL");
     s->op_warp = (k && std::strcmp(k, "tma") == 0) ? 0 : 1;
     s->op_cta = (k && std::strcmp(k, "warp") == 0) ? 0 : 1;
-    s->op_split = (k && std::strcmp(k, "split") == 0) ? 1 : 0;
     const char* mi = std::getenv("STDG_MIXED_INNER");   // binary32 iterations per outer mixed step
     if (mi && std::atoi(mi) > 0 && std::atoi(mi) <= 1000) s->mix_inner = s->mix_inner_mg = std::atoi(mi);
     const char* mm = std::getenv("STDG_MIXED_M");       // directions kept by the outer flexible CG

@@ -763,210 +763,6 @@ __global__ void __launch_bounds__(32 * WPC) k_apply_cta(WarpArgs a, const typena
   }
 }
 
-// binary32 blocks, one warp per tet, with the tet's five blocks staged in two halves on two
-// mbarriers (the diagonal block and the first two face blocks with the x rows; the last two face
-// blocks) and the x rows double-buffered: as soon as the warp has finished with one half of this
-// tet, that half of the next tet is on its way, so each warp keeps copies in flight while it
-// computes (the single-stage warp kernel waits for a whole tet after finishing the previous one).
-// Products, rows 32..N-1 and the row epilogue as in k_apply_warp.
-template <int NG, int NC>
-__global__ void __launch_bounds__(128, 1) k_apply_split(WarpArgs a, const float* __restrict__ x, float* __restrict__ y) {
-  constexpr int N = NC, NR = warp_nr_c(NC), NP = warp_np_c(NC), Nst = NC * NG, ZR = 5 * NG * NR;
-  constexpr int kBlk = NR * NP;                   // floats per padded block
-  extern __shared__ __align__(128) unsigned char wsm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  unsigned char* base = wsm + (size_t)warp * a.warp_bytes;
-  float* blk = reinterpret_cast<float*>(base);                         // 5 blocks
-  float* xz = reinterpret_cast<float*>(base + 5 * kBlk * sizeof(float));   // 2 x [slot][q][NR]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + a.bar_off);      // [0]: blocks 0..2 + x, [1]: blocks 3..4
-  const float scale = (float)a.scale;
-  const bool has_mass = a.mass_coef != 0.0, kron = a.kron != 0, pinned = a.pinned != 0;
-  float tacc[NG * NG];
-#pragma unroll
-  for (int c = 0; c < NG * NG; ++c) tacc[c] = (float)a.Tacc[c];
-  for (int e = lane; e < 2 * ZR; e += 32) xz[e] = 0.0f;   // padding entries stay 0
-  if (lane == 0) {
-    mbar_init(&bar[0], 33);                       // lane 0's expect_tx + 32 cp.async arrivals
-    mbar_init(&bar[1], 1);                        // lane 0's expect_tx
-    fence_async_smem();
-  }
-  __syncwarp();
-  const unsigned char* Bd = static_cast<const unsigned char*>(a.Bd);
-  const unsigned char* Ao = static_cast<const unsigned char*>(a.Ao);
-  // half 0: slots 0..2 and the x rows into buffer xb; half 1: slots 3..4
-  auto issue = [&](int i, int half, int xb) {
-    const int4 gf = a.gface[i], gn = a.gnbr[i];
-    if (lane == 0) {
-      uint32_t bytes = 0;
-      const int s0 = half ? 3 : 0, s1 = half ? 5 : 3;
-      for (int sl = s0; sl < s1; ++sl)
-        if (sl == 0 || pick4(gf, sl - 1) >= 0) bytes += a.blk_bytes;
-      fence_async_smem();                         // earlier generic reads of these slots before the copies
-      mbar_expect_tx(&bar[half], bytes);
-      for (int sl = s0; sl < s1; ++sl) {
-        if (sl > 0 && pick4(gf, sl - 1) < 0) continue;
-        const unsigned char* src = sl == 0 ? Bd + (size_t)i * a.blk_bytes : Ao + (size_t)(pick4(gf, sl - 1) >> 1) * a.blk_bytes;
-        tma_load_1d(blk + sl * kBlk, src, a.blk_bytes, &bar[half]);
-      }
-    }
-    if (half == 0) {
-      float* zb = xz + xb * ZR;
-      for (int idx = lane; idx < 5 * NG * N; idx += 32) {
-        const int rw = idx / N, l = idx - rw * N, sl = rw / NG;
-        const int nb = slot_tet(i, sl, gf, gn);
-        if (nb >= 0) cp_async<4>(zb + rw * NR + l, x + (size_t)nb * Nst + (rw - sl * NG) * N + l);
-      }
-      cp_async_mbar_arrive_noinc(&bar[0]);
-    }
-  };
-  auto wait_bar = [&](int half, uint32_t par) -> bool {
-    long spins = 0;
-    while (!mbar_wait_hint(&bar[half], par))
-      if (++spins > kWarpSpin) return false;
-    return true;
-  };
-  const int nw = gridDim.x * wpc;
-  float dacc[NG];
-#pragma unroll
-  for (int q = 0; q < NG; ++q) dacc[q] = 0.0f;
-  int i = blockIdx.x * wpc + warp, it = 0;
-  bool abort = false;
-  // uses of each half's mbarrier: issued and waited for (the phase parity of a wait is waited & 1)
-  int iss0 = 0, iss1 = 0, wt0 = 0, wt1 = 0;
-  if (i < a.ne) { issue(i, 0, 0); issue(i, 1, 0); iss0 = iss1 = 1; }
-  for (; i < a.ne; i += nw, ++it) {
-    const int inx = i + nw;
-    float* zb = xz + (it & 1) * ZR;
-    const int4 gf = a.gface[i], gn = a.gnbr[i];
-    int pres = 1, trm = 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const int fj = pick4(gf, f);
-      pres |= (fj >= 0 ? 1 : 0) << (f + 1);
-      trm |= (fj >= 0 && (fj & 1) ? 1 : 0) << (f + 1);
-    }
-    if (__any_sync(0xffffffffu, !wait_bar(0, (uint32_t)(wt0 & 1)))) { abort = true; break; }
-    ++wt0;
-    __syncwarp();
-    if (pinned && lane < 5 * NG) {                // pinned entries (constant mode of tet 0) read as 0
-      if (slot_tet(i, lane / NG, gf, gn) == 0) zb[lane * NR] = 0.0f;
-    }
-    __syncwarp();
-    const int k = lane;
-    const bool main_row = lane < (N < 32 ? N : 32);
-    const int g = lane >> 3, c = lane & 7, r = 32 + g;
-    float2 c0[NG], c1[NG], ec[NG];
-#pragma unroll
-    for (int q = 0; q < NG; ++q) c0[q] = c1[q] = ec[q] = make_float2(0.0f, 0.0f);
-    // products of slot sl: main rows by lane, rows 32..N-1 by 8-lane groups
-    auto slot_products = [&](int sl) {
-      if (!((pres >> sl) & 1)) return;
-      const float* B = blk + sl * kBlk;
-      const float* z = zb + sl * NG * NR;
-      const bool tr = (trm >> sl) & 1;
-      if (main_row) {
-        if (!tr) {
-#pragma unroll
-          for (int l = 0; l < NR; l += 8) {
-            warp_chunk2<NG>(B + k * NP + l, 1, z + l, NR, c0);
-            if (l + 4 < NR) warp_chunk2<NG>(B + k * NP + l + 4, 1, z + l + 4, NR, c1);
-          }
-        } else {
-#pragma unroll
-          for (int l = 0; l < NR; l += 8) {
-            warp_chunk2<NG>(B + l * NP + k, NP, z + l, NR, c0);
-            if (l + 4 < NR) warp_chunk2<NG>(B + (l + 4) * NP + k, NP, z + l + 4, NR, c1);
-          }
-        }
-      }
-      if (N > 32 && r < N) {
-        for (int ch = c; ch < NR / 4; ch += 8) {
-          const int l = 4 * ch;
-          if (!tr) warp_chunk2<NG>(B + r * NP + l, 1, z + l, NR, ec);
-          else warp_chunk2<NG>(B + l * NP + r, NP, z + l, NR, ec);
-        }
-      }
-    };
-#pragma unroll
-    for (int sl = 0; sl < 3; ++sl) slot_products(sl);
-    __syncwarp();
-    if (inx < a.ne) { issue(inx, 0, (it + 1) & 1); ++iss0; }     // slots 0..2 and x of the next tet
-    if (__any_sync(0xffffffffu, !wait_bar(1, (uint32_t)(wt1 & 1)))) { abort = true; break; }
-    ++wt1;
-    __syncwarp();
-#pragma unroll
-    for (int sl = 3; sl < 5; ++sl) slot_products(sl);
-    __syncwarp();
-    if (inx < a.ne) { issue(inx, 1, 0); ++iss1; }                  // slots 3..4 of the next tet
-    auto finish = [&](int kk, const float (&v)[NG]) {
-#pragma unroll
-      for (int q = 0; q < NG; ++q) {
-        float o = v[q];
-        if (!kron) {
-          o = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NG; ++b) o += tacc[q * NG + b] * v[b];
-        }
-        o *= scale;
-        if (has_mass) {
-          float m = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NG; ++b) m += (float)a.Kmass[q * NG + b] * zb[b * NR + kk];
-          o += (float)(a.mass_coef * a.detJ[i]) * m;
-        }
-        if (pinned && i == 0 && kk == 0) o = (float)a.pin_diag * x[q * N];
-        y[(size_t)i * Nst + q * N + kk] = o;
-        if (a.dotpart) dacc[q] += x[(size_t)i * Nst + q * N + kk] * o;
-      }
-    };
-    if (main_row) {
-      float v[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) v[q] = (c0[q].x + c0[q].y) + (c1[q].x + c1[q].y);
-      finish(k, v);
-    }
-    if (N > 32) {
-      float v[NG];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) {
-        float h = ec[q].x + ec[q].y;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-        v[q] = h;
-      }
-      if (c == 0 && r < N) finish(r, v);
-    }
-    __syncwarp();                                 // the x buffer of this tet is refilled two tets later
-  }
-  if (a.dotpart) {                                // fixed order: lanes by shuffle, warps by index
-    __shared__ float wdot[4][kMaxNg];
-#pragma unroll
-    for (int q = 0; q < NG; ++q) {
-      float v = dacc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wdot[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NG) {
-      double t = 0.0;
-      for (int w = 0; w < wpc; ++w) t += (double)wdot[w][threadIdx.x];
-      a.dotpart[(size_t)blockIdx.x * NG + threadIdx.x] = t;
-    }
-  }
-  if (abort) {
-    if (lane == 0) atomicExch(a.err, 1);
-    // bounded waits for the copies still in flight: each half's issued and not yet waited phase
-    long spins = 0;
-    if (iss0 > wt0)
-      while (!mbar_wait_hint(&bar[0], (uint32_t)(wt0 & 1)) && ++spins < kWarpSpin) {
-      }
-    spins = 0;
-    if (iss1 > wt1)
-      while (!mbar_wait_hint(&bar[1], (uint32_t)(wt1 & 1)) && ++spins < kWarpSpin) {
-      }
-  }
-}
-
 // padded block copies: dst block b = planes x NR x NP, zero outside N x N
 template <typename TB, int PLANES>
 __global__ void k_to_padded(int64_t nblk, int N, int NR, int NP, const double* __restrict__ src, TB* __restrict__ dst,
@@ -1057,19 +853,6 @@ constexpr int kCtaWarps = 4;
 // share among warps (N = 35: 19.2 -> 11.7 ms per application at 384,000 tets, the warp kernel fitting
 // three warps per SM); for the binary32 policies and at N <= 20 the per-tet work is too short for
 // three CTA barriers and the serial row pass (measured 1.4-2x slower), so the warp kernels serve.
-// split-stage binary32 kernel (STDG_OP_KERNEL=split) at N = 20 and 35
-template <typename W>
-static bool use_split(const stdg_solver* s) {
-  return s->op_split != 0 && W::kPlanes == 1 && sizeof(typename W::TB) == 4 && (s->N == 20 || s->N == 35);
-}
-// per warp: 5 block slots, two x buffers [slot][q][NR], two mbarriers
-static WarpArgs split_layout(const stdg_solver* s) {
-  WarpArgs a = warp_layout(s, sizeof(float), 1, sizeof(float), 1);
-  a.bar_off = a16((size_t)5 * a.blk_bytes + (size_t)2 * 5 * s->Ng * a.NR * sizeof(float));
-  a.warp_bytes = a16(a.bar_off + 2 * sizeof(uint64_t));
-  return a;
-}
-
 template <typename W>
 static bool use_cta(const stdg_solver* s) {
   return s->op_cta != 0 && W::kPlanes == 2 && s->N > 20;
@@ -1077,7 +860,6 @@ static bool use_cta(const stdg_solver* s) {
 
 template <typename W>
 static WarpArgs warp_args(const stdg_solver* s) {
-  if (use_split<W>(s)) return split_layout(s);
   if (use_cta<W>(s)) {
     // two stages when two CTAs fit on an SM with them, else one
     WarpArgs a = cta_layout(s, sizeof(typename W::TB), W::kPlanes, sizeof(typename W::XIn), 2, kCtaWarps);
@@ -1100,12 +882,9 @@ using WarpKernel = void (*)(WarpArgs, const typename W::XIn*, typename W::YOut*)
 // the instantiation for this N: compile-time N for p = 2, 3, 4, runtime N otherwise (CTA kernels:
 // pair policy only, see use_cta)
 template <typename W, int NG>
-static WarpKernel<W> warp_kernel(int N, bool cta, bool split = false) {
+static WarpKernel<W> warp_kernel(int N, bool cta) {
   if constexpr (W::kPlanes == 2) {
     if (cta) return N == 35 ? k_apply_cta<W, NG, 35, kCtaWarps> : k_apply_cta<W, NG, 0, kCtaWarps>;
-  }
-  if constexpr (W::kPlanes == 1 && sizeof(typename W::TB) == 4) {
-    if (split) return N == 35 ? k_apply_split<NG, 35> : k_apply_split<NG, 20>;
   }
   switch (N) {
     case 10: return k_apply_warp<W, NG, 10>;
@@ -1120,7 +899,7 @@ static WarpKernel<W> warp_kernel(int N, bool cta, bool split = false) {
 template <typename W, int NG>
 static cudaError_t warp_configure(stdg_solver* s) {
   const WarpArgs a = warp_args<W>(s);
-  const WarpKernel<W> kern = warp_kernel<W, NG>(s->N, use_cta<W>(s), use_split<W>(s));
+  const WarpKernel<W> kern = warp_kernel<W, NG>(s->N, use_cta<W>(s));
   int& grid = s->warp_grid[warp_kind<W>() * 8 + NG];
   int& wpc = s->warp_wpc[warp_kind<W>() * 8 + NG];
   if (grid != 0) return cudaSuccess;
@@ -1173,7 +952,7 @@ static cudaError_t launch_warp_ng(stdg_solver* s, const WarpArgs& a, const typen
   if (grid == 0) return cudaErrorNotReady;                  // warp_prepare has not run
   const bool cta = use_cta<W>(s);
   const size_t smem = cta ? (size_t)a.warp_bytes : (size_t)wpc * a.warp_bytes;
-  warp_kernel<W, NG>(s->N, cta, use_split<W>(s))<<<grid, 32 * wpc, smem, s->stream>>>(a, x, y);
+  warp_kernel<W, NG>(s->N, cta)<<<grid, 32 * wpc, smem, s->stream>>>(a, x, y);
   return cudaGetLastError();
 }
 

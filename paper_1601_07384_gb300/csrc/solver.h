@@ -56,7 +56,6 @@ struct stdg_solver {
   int warp_grid[32] = {0}, warp_wpc[32] = {0};
   int op_warp = 1;                            // 1: warp-per-tet kernels, 0: block-staged TMA kernels
   int op_cta = 1;                             // with op_warp: several warps share each staged tet
-  int op_split = 0;                           // binary32: a tet's blocks staged in two halves
   int mix_inner = 80;                         // binary32 CG iterations per outer step of the mixed solve
   int mix_inner_mg = 40;                      // the same with the coarse correction (converges faster)
   int mix_m = 16;                             // directions the outer flexible CG keeps

@@ -432,14 +432,13 @@ def test_step_with_previous_viscous_solvers():
     assert "2 passed" in r.stdout
 
 
-@pytest.mark.parametrize("kernel", ["tma", "warp", "split"])
+@pytest.mark.parametrize("kernel", ["tma", "warp"])
 @pytest.mark.parametrize("p,pt", [(3, 1), (4, 4)])
 @pytest.mark.parametrize("prec,tol", [("mixed_f32", 4e-6), ("df32", 1e-12)])
 def test_alternative_operator_kernels_match_oracle(kernel, p, pt, prec, tol, monkeypatch):
     """STDG_OP_KERNEL selects the operator kernels kept for comparison with the default ones: "warp"
-    (one warp per staged tet, also for the pair policy at N = 35), "split" (binary32: a tet's blocks
-    staged in two halves, the next tet's half refilled as soon as this one is done with it) and "tma"
-    (block-staged TMA kernels).  The same operator (Eq. CS_19) to the same tolerances as the default kernels, at
+    (one warp per staged tet, also for the pair policy at N = 35) and "tma" (block-staged TMA
+    kernels).  The same operator (Eq. CS_19) to the same tolerances as the default kernels, at
     the benchmarked degrees; the pinned solver of the pressure system, so the pin rows are covered."""
     monkeypatch.setenv("STDG_OP_KERNEL", kernel)
     gs, d = setup(2, p, pt, precision=prec)
