@@ -512,11 +512,17 @@ def main():
     tcur = C.c_double(tw)
     barrier()
     te0 = time.perf_counter()
+    t_h2d = t_d2h = 0.0                           # the state copies, to separate them from the steps
     for _ in range(ne2e):
+        tc0 = time.perf_counter()
         g._lib.check(lib.stdg_set_state(solver._h, C.c_void_p(Pin.data_ptr()), C.c_void_p(Vin.data_ptr()), 0, tw))
+        tc1 = time.perf_counter()
         solver.step(w["nu"], w["npic"], method=args.solver, tol=w["tol"])
+        tc2 = time.perf_counter()
         g._lib.check(lib.stdg_get_state(solver._h, C.c_void_p(Ph.data_ptr()), C.c_void_p(Vh.data_ptr()), 0,
                                         C.byref(tcur)))
+        t_h2d += tc1 - tc0
+        t_d2h += time.perf_counter() - tc2
     barrier()
     e2e = (time.perf_counter() - te0) / ne2e
 
@@ -575,7 +581,8 @@ def main():
                    "l2": "inputs larger than L2 (operator blocks + Q per step >> 129 MB)"},
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "s/step", "h2d_bytes_per_step": int(Pin.numel() + Vin.numel()) * 8,
-                "d2h_bytes_per_step": int(Ph.numel() + Vh.numel()) * 8, "steps": ne2e},
+                "d2h_bytes_per_step": int(Ph.numel() + Vh.numel()) * 8, "steps": ne2e,
+                "h2d_s_per_step": t_h2d / ne2e, "d2h_s_per_step": t_d2h / ne2e},
         "gpu_launches": int(prof["kernel_launches"]),
         "operator_applications_per_step": ops_per_step,
         "press_iters": [s["press_iters"] for s in stats],

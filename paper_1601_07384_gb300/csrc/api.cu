@@ -376,10 +376,11 @@ extern "C" stdg_status stdg_get_blocks(const stdg_solver* s, double* Q, double* 
 extern "C" stdg_status stdg_get_state(const stdg_solver* s, double* P, double* V, int on_device, double* t) {
   if (!s) { set_error("NULL solver"); return STDG_EINVAL; }
   cudaSetDevice(s->device);
-  cudaStreamSynchronize(s->stream);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (P) STDG_CUDA(cudaMemcpy(P, s->P, s->ne * s->Nst * sizeof(double), k));
-  if (V) STDG_CUDA(cudaMemcpy(V, s->V, s->nf * 3 * s->Nst * sizeof(double), k));
+  // on the solver's stream, after its work, then wait: the caller reads the buffers on return
+  if (P) STDG_CUDA(cudaMemcpyAsync(P, s->P, s->ne * s->Nst * sizeof(double), k, s->stream));
+  if (V) STDG_CUDA(cudaMemcpyAsync(V, s->V, s->nf * 3 * s->Nst * sizeof(double), k, s->stream));
+  STDG_CUDA(cudaStreamSynchronize(s->stream));
   if (t) *t = s->t;
   return STDG_OK;
 }
@@ -387,10 +388,11 @@ extern "C" stdg_status stdg_get_state(const stdg_solver* s, double* P, double* V
 extern "C" stdg_status stdg_set_state(stdg_solver* s, const double* P, const double* V, int on_device, double t) {
   stdg_status e = check(s);
   if (e != STDG_OK) return e;
-  cudaStreamSynchronize(s->stream);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (P) STDG_CUDA(cudaMemcpy(s->P, P, s->ne * s->Nst * sizeof(double), k));
-  if (V) STDG_CUDA(cudaMemcpy(s->V, V, s->nf * 3 * s->Nst * sizeof(double), k));
+  // on the solver's stream, after its work, then wait: the caller may reuse the buffers on return
+  if (P) STDG_CUDA(cudaMemcpyAsync(s->P, P, s->ne * s->Nst * sizeof(double), k, s->stream));
+  if (V) STDG_CUDA(cudaMemcpyAsync(s->V, V, s->nf * 3 * s->Nst * sizeof(double), k, s->stream));
+  STDG_CUDA(cudaStreamSynchronize(s->stream));
   s->t = t;
   return STDG_OK;
 }
