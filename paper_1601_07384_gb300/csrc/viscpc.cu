@@ -18,6 +18,9 @@
 #include <complex>
 #include <vector>
 
+#include <type_traits>
+
+#include "lp_ptx.cuh"
 #include "solver.h"
 
 namespace stdg {
@@ -238,15 +241,22 @@ __global__ void __launch_bounds__(256) k_visc_fd_t(int ne, const float* __restri
   for (int i0 = blockIdx.x * TB; i0 < ne; i0 += gridDim.x * TB) {
     const int nt = min(TB, ne - i0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nt * Nst; idx += blockDim.x) vs[idx] = (float)r[(size_t)i0 * Nst + idx];
+    // the pass's U blocks (and binary32 rows) by cp.async: every thread issues all its copies before
+    // waiting once (copies through registers, one load after another, left the kernel waiting on
+    // memory latency: N^2 = 1225 at p = 4 is not a multiple of 4, so those went one word at a time)
     const float* Ug = U + (size_t)i0 * NN;
-    if (NN % 4 == 0) {
-      const float4* U4 = reinterpret_cast<const float4*>(Ug);
-      float4* u4 = reinterpret_cast<float4*>(us);
-      for (int idx = threadIdx.x; idx < nt * NN / 4; idx += blockDim.x) u4[idx] = U4[idx];
+    if constexpr (NN % 4 == 0) {
+      for (int idx = threadIdx.x; idx < nt * NN / 4; idx += blockDim.x) cp_async<16>(us + 4 * idx, Ug + 4 * idx);
     } else {
-      for (int idx = threadIdx.x; idx < nt * NN; idx += blockDim.x) us[idx] = Ug[idx];
+      for (int idx = threadIdx.x; idx < nt * NN; idx += blockDim.x) cp_async<4>(us + idx, Ug + idx);
     }
+    if constexpr (std::is_same<TI, float>::value) {
+      for (int idx = threadIdx.x; idx < nt * Nst; idx += blockDim.x) cp_async<4>(vs + idx, r + (size_t)i0 * Nst + idx);
+    } else {
+      for (int idx = threadIdx.x; idx < nt * Nst; idx += blockDim.x) vs[idx] = (float)r[(size_t)i0 * Nst + idx];
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int i = i0 + tl;
     const bool act = tl < nt;
@@ -314,15 +324,37 @@ __global__ void __launch_bounds__(256) k_visc_fd_t(int ne, const float* __restri
   }
 }
 
+// Resident blocks of a kernel across the device (its grid-stride loop then splits the work evenly: a
+// fixed 8 blocks per SM with 5 resident ran 1.6 waves, the last at 60 % occupancy).  Host-side query,
+// no stream work (safe while a graph is being captured); cached per kernel.
+template <typename K>
+static int resident_grid(K kern, int threads, size_t smem) {
+  static int cached = 0;
+  if (cached) return cached;
+  int dev = 0, nsm = 152, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+  cached = nsm * per;
+  return cached;
+}
+
+template <int N, int NG, typename TI, typename TO>
+static void launch_fd_ng(cudaStream_t st, int ne, const float* U, const float* lam, const double* detJ,
+                         const SmallK& K, float c, const TI* r, TO* z, int accum) {
+  const int blocks = resident_grid(k_visc_fd_t<N, NG, TI, TO>, 256, 0);
+  k_visc_fd_t<N, NG, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum);
+}
+
 template <int N, typename TI, typename TO>
-static void launch_fd_t(int Ng, int blocks, cudaStream_t st, int ne, const float* U, const float* lam,
+static void launch_fd_t(int Ng, int, cudaStream_t st, int ne, const float* U, const float* lam,
                         const double* detJ, const SmallK& K, float c, const TI* r, TO* z, int accum) {
   switch (Ng) {
-    case 1: k_visc_fd_t<N, 1, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 2: k_visc_fd_t<N, 2, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 3: k_visc_fd_t<N, 3, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    case 4: k_visc_fd_t<N, 4, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
-    default: k_visc_fd_t<N, 5, TI, TO><<<blocks, 256, 0, st>>>(ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 1: launch_fd_ng<N, 1>(st, ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 2: launch_fd_ng<N, 2>(st, ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 3: launch_fd_ng<N, 3>(st, ne, U, lam, detJ, K, c, r, z, accum); break;
+    case 4: launch_fd_ng<N, 4>(st, ne, U, lam, detJ, K, c, r, z, accum); break;
+    default: launch_fd_ng<N, 5>(st, ne, U, lam, detJ, K, c, r, z, accum); break;
   }
 }
 
